@@ -1,0 +1,308 @@
+"""FP64 CPU oracle of the parallel heat method (arXiv 1812.06060).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users.  The product path never
+imports this package.  The arithmetic lives in ``geoheat_oracle.c`` (plain,
+single-threaded C, one function per step of the paper); this module compiles
+it with gcc, loads it with ctypes and chains the steps of Algorithm 1.
+
+Parity status of each function (pins in tests/test_oracle_*.py):
+  connectivity, geometry, bfs, gs, normalize, face_admm, edge_admm,
+  integrate_face, integrate_edge: pinned.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "geoheat_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libgeoheat_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MU = 100.0          # penalty parameter, Sec. 3.2 and Sec. 4.1
+ADMM_ITERS = 10     # I_max, Sec. 6
+ZERO_EXP = -(1 << 28)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE double: no fast-math, no FMA
+    contraction) into oracle/_build."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+P = C.c_void_p
+I64 = C.c_int64
+I32 = C.c_int32
+D = C.c_double
+
+
+def _declare(L):
+    L.orc_edges.restype = I64
+    L.orc_edges.argtypes = [I64, I64, P, P]
+    L.orc_connectivity.restype = C.c_int
+    L.orc_connectivity.argtypes = [I64, I64, P, I64, P, P, P, P, P, P, P, P, P]
+    L.orc_geometry.restype = C.c_int
+    L.orc_geometry.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, P]
+    L.orc_bfs.restype = C.c_int
+    L.orc_bfs.argtypes = [I64, P, P, I64, P, P, P, P, P]
+    L.orc_gs.restype = C.c_int
+    L.orc_gs.argtypes = [I64, P, P, P, P, P, D, P, P, I32, I32, P, P]
+    L.orc_gs_plain.restype = C.c_int
+    L.orc_gs_plain.argtypes = [I64, P, P, P, P, P, D, P, P, I32, I32, P]
+    L.orc_heat_residual.restype = D
+    L.orc_heat_residual.argtypes = [I64, P, P, P, P, P, D, P, P, P]
+    L.orc_normalize.restype = C.c_int
+    L.orc_normalize.argtypes = [I64, P, I64, P, P, P, P]
+    L.orc_face_admm.restype = C.c_int
+    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, P, P, P, P]
+    L.orc_edge_admm.restype = C.c_int
+    L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, P, P, P, P, P]
+    L.orc_integrate_face.restype = C.c_int
+    L.orc_integrate_face.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
+    L.orc_integrate_edge.restype = C.c_int
+    L.orc_integrate_edge.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise OracleError(f"{what} failed with code {rc}")
+    return rc
+
+
+@dataclass
+class MeshData:
+    """Connectivity and geometry of one mesh (Sec. 3, Sec. 3.1, Sec. 4.1)."""
+    P: np.ndarray
+    F: np.ndarray
+    edges: np.ndarray
+    flip: np.ndarray | None
+    face_edge: np.ndarray
+    face_sign: np.ndarray
+    edge_face: np.ndarray
+    edge_slot: np.ndarray
+    rowptr: np.ndarray
+    col: np.ndarray
+    col_edge: np.ndarray
+    Af: np.ndarray
+    Av: np.ndarray
+    cot: np.ndarray
+    theta: np.ndarray
+    hbar: float
+
+    @property
+    def nv(self):
+        return self.P.shape[0]
+
+    @property
+    def nf(self):
+        return self.F.shape[0]
+
+    @property
+    def ne(self):
+        return self.edges.shape[0]
+
+
+def mesh_data(V, F, flip=None) -> MeshData:
+    """Connectivity (orc_edges, orc_connectivity) and geometry (orc_geometry)."""
+    L = lib()
+    P_ = np.ascontiguousarray(V, dtype=np.float64)
+    F_ = np.ascontiguousarray(F, dtype=np.int32)
+    nv, nf = P_.shape[0], F_.shape[0]
+    edges = np.empty((3 * nf, 2), np.int32)
+    ne = _check(L.orc_edges(nv, nf, _p(F_), _p(edges)), "orc_edges")
+    edges = np.ascontiguousarray(edges[:ne])
+    if flip is not None:
+        flip = np.ascontiguousarray(flip, dtype=np.uint8)
+        assert flip.shape == (ne,)
+    face_edge = np.empty((nf, 3), np.int32)
+    face_sign = np.empty((nf, 3), np.int8)
+    edge_face = np.empty((ne, 2), np.int32)
+    edge_slot = np.empty((ne, 2), np.int32)
+    rowptr = np.empty(nv + 1, np.int32)
+    col = np.empty(2 * ne, np.int32)
+    col_edge = np.empty(2 * ne, np.int32)
+    _check(L.orc_connectivity(nv, nf, _p(F_), ne, _p(edges), _p(flip), _p(face_edge), _p(face_sign),
+                              _p(edge_face), _p(edge_slot), _p(rowptr), _p(col), _p(col_edge)),
+           "orc_connectivity")
+    Af = np.empty(nf)
+    Av = np.empty(nv)
+    cot = np.empty((nf, 3))
+    theta = np.empty(ne)
+    hbar = C.c_double(0.0)
+    _check(L.orc_geometry(nv, _p(P_), nf, _p(F_), ne, _p(edges), _p(edge_face), _p(edge_slot), _p(Af),
+                          _p(Av), _p(cot), _p(theta), C.byref(hbar)), "orc_geometry")
+    return MeshData(P_, F_, edges, flip, face_edge, face_sign, edge_face, edge_slot, rowptr, col, col_edge,
+                    Af, Av, cot, theta, hbar.value)
+
+
+@dataclass
+class BFS:
+    level: np.ndarray
+    parent: np.ndarray
+    order: np.ndarray
+    level_off: np.ndarray
+    nlev: int
+
+
+def bfs(md: MeshData, sources) -> BFS:
+    """Breadth-first vertex sets and pairing (eq. VertexSets, Sec. 3.3)."""
+    src = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)
+    nv = md.nv
+    level = np.empty(nv, np.int32)
+    parent = np.empty(nv, np.int32)
+    order = np.full(nv, -1, np.int32)
+    level_off = np.empty(nv + 1, np.int32)
+    nlev = _check(lib().orc_bfs(nv, _p(md.rowptr), _p(md.col), src.size, _p(src), _p(level), _p(parent),
+                                _p(order), _p(level_off)), "orc_bfs")
+    nreach = int(level_off[nlev])
+    return BFS(level, parent, order[:nreach].copy(), level_off[:nlev + 1].copy(), nlev)
+
+
+def gs(md: MeshData, b: BFS, t: float, sweeps: int, state=None):
+    """Gauss-Seidel heat diffusion (eq. HeatDiffusionUpdate).  Returns the
+    state (um, ue) with u = um * 2^ue; ``state`` resumes from a previous one
+    (default u = 0)."""
+    if state is None:
+        um = np.zeros(md.nv)
+        ue = np.full(md.nv, ZERO_EXP, np.int32)
+    else:
+        um, ue = state[0].copy(), state[1].copy()
+    _check(lib().orc_gs(md.nv, _p(md.rowptr), _p(md.col), _p(md.col_edge), _p(md.theta), _p(md.Av), t,
+                        _p(b.order), _p(b.level_off), b.nlev, sweeps, _p(um), _p(ue)), "orc_gs")
+    return um, ue
+
+
+def gs_plain(md: MeshData, b: BFS, t: float, sweeps: int, u=None):
+    u = np.zeros(md.nv) if u is None else np.ascontiguousarray(u, dtype=np.float64).copy()
+    _check(lib().orc_gs_plain(md.nv, _p(md.rowptr), _p(md.col), _p(md.col_edge), _p(md.theta), _p(md.Av), t,
+                              _p(b.order), _p(b.level_off), b.nlev, sweeps, _p(u)), "orc_gs_plain")
+    return u
+
+
+def heat_residual(md: MeshData, b: BFS, t: float, state) -> float:
+    um, ue = state
+    return lib().orc_heat_residual(md.nv, _p(md.rowptr), _p(md.col), _p(md.col_edge), _p(md.theta), _p(md.Av),
+                                   t, _p(b.level), _p(um), _p(ue))
+
+
+def normalize(md: MeshData, state) -> np.ndarray:
+    """h = -grad u / |grad u| per face (eq. HeatDiffusionNormalization)."""
+    um, ue = state
+    um = np.ascontiguousarray(um, dtype=np.float64)
+    ue = np.ascontiguousarray(ue, dtype=np.int32)
+    h = np.empty((md.nf, 3))
+    _check(lib().orc_normalize(md.nv, _p(md.P), md.nf, _p(md.F), _p(um), _p(ue), _p(h)), "orc_normalize")
+    return h
+
+
+def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU):
+    """Face-based ADMM (Sec. 3.2).  Returns g [nf,3], y [nf,3,3],
+    lambda [nf,3,3] (NaN on boundary slots) and residuals [iters, 3]."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    g = np.empty((md.nf, 3))
+    y = np.empty((md.nf, 3, 3))
+    lam = np.empty((md.nf, 3, 3))
+    res = np.empty((max(iters, 1), 3))
+    _check(lib().orc_face_admm(md.nv, _p(md.P), md.nf, md.ne, _p(md.edges), _p(md.face_edge), _p(md.edge_face),
+                               _p(md.edge_slot), _p(md.Af), _p(h), iters, mu, _p(g), _p(y), _p(lam), _p(res)),
+           "orc_face_admm")
+    return g, y, lam, res[:iters]
+
+
+def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU):
+    """Edge-based ADMM (Sec. 4.1).  Returns x [ne], w [nf,3], lambda [nf,3],
+    z [nf,3] and residuals [iters, 2]."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    x = np.empty(md.ne)
+    w = np.empty((md.nf, 3))
+    lam = np.empty((md.nf, 3))
+    z = np.empty((md.nf, 3))
+    res = np.empty((max(iters, 1), 2))
+    _check(lib().orc_edge_admm(md.nv, _p(md.P), md.nf, _p(md.F), md.ne, _p(md.edges), _p(md.flip),
+                               _p(md.face_edge), _p(md.face_sign), _p(md.edge_face), _p(md.edge_slot), _p(h),
+                               iters, mu, _p(x), _p(w), _p(lam), _p(z), _p(res)), "orc_edge_admm")
+    return x, w, lam, z, res[:iters]
+
+
+def integrate_face(md: MeshData, b: BFS, g, parent=None) -> np.ndarray:
+    """Breadth-first integration of face gradients (eq. IntegrationStep)."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    par = np.ascontiguousarray(b.parent if parent is None else parent, dtype=np.int32)
+    d = np.empty(md.nv)
+    _check(lib().orc_integrate_face(md.nv, _p(md.P), _p(md.rowptr), _p(md.col), _p(md.col_edge),
+                                    _p(md.edge_face), _p(b.order), _p(b.level_off), b.nlev, _p(par), _p(g),
+                                    _p(d)), "orc_integrate_face")
+    return d
+
+
+def integrate_edge(md: MeshData, b: BFS, x, parent=None) -> np.ndarray:
+    """Breadth-first integration of edge differences (Sec. 4)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    par = np.ascontiguousarray(b.parent if parent is None else parent, dtype=np.int32)
+    d = np.empty(md.nv)
+    _check(lib().orc_integrate_edge(md.nv, _p(md.edges), _p(md.flip), _p(md.rowptr), _p(md.col),
+                                    _p(md.col_edge), _p(b.order), _p(b.level_off), b.nlev, _p(par), _p(x),
+                                    _p(d)), "orc_integrate_edge")
+    return d
+
+
+def diffusion_time(md: MeshData, m: float = 1.0) -> float:
+    """t = m * hbar^2 (eq. DiffusionTime)."""
+    return m * md.hbar * md.hbar
+
+
+def solve(md: MeshData, sources, form: str = "edge", sweeps: int = 200, m: float = 1.0, t: float | None = None,
+          admm_iters: int = ADMM_ITERS, mu: float = MU) -> dict:
+    """Algorithm 1 end to end: Diffusion -> normalise -> Integrable ->
+    Recovery, in the face form (Sec. 3) or the edge form (Sec. 4).  Returns
+    every intermediate."""
+    t = diffusion_time(md, m) if t is None else t
+    b = bfs(md, sources)
+    st = gs(md, b, t, sweeps)
+    h = normalize(md, st)
+    out = {"t": t, "bfs": b, "u": st, "h": h}
+    if form == "face":
+        g, y, lam, res = face_admm(md, h, admm_iters, mu)
+        out.update(g=g, res=res, d=integrate_face(md, b, g))
+    elif form == "edge":
+        x, w, lam, z, res = edge_admm(md, h, admm_iters, mu)
+        out.update(x=x, z=z, res=res, d=integrate_edge(md, b, x))
+    else:
+        raise ValueError(form)
+    return out
+
+
+def u_float(state) -> np.ndarray:
+    """u = m * 2^e as plain doubles (underflows to 0 far from the sources)."""
+    um, ue = state
+    return np.ldexp(um, np.clip(ue, -2000, 2000))

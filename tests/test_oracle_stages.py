@@ -1,0 +1,174 @@
+"""Oracle normalisation (eq. HeatDiffusionNormalization), face-based ADMM
+(Sec. 3.2), edge-based ADMM (Sec. 4.1) and integration (Sec. 3.3, Sec. 4)."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+import oracle.hm as hm
+
+
+def _planar(N=11, seed=6):
+    m = meshgen.jittered_grid(N, seed)
+    return m, oracle.mesh_data(m.V, m.F)
+
+
+# ---------------------------------------------------------------- normalise
+
+def test_normalize_linear_field():
+    """u = a.p + c on a planar mesh has the exact gradient a on every face."""
+    m, md = _planar()
+    a = np.array([0.3, -1.7, 0.0])
+    u = m.V @ a + 5.0
+    ex = np.zeros(md.nv, np.int32)
+    um, ue = np.frexp(u)
+    h = oracle.normalize(md, (um, ue.astype(np.int32)))
+    assert np.allclose(h, -a / np.linalg.norm(a), atol=1e-13)
+    # a common power-of-two scale is invisible
+    h2 = oracle.normalize(md, (um, (ue - 3000).astype(np.int32)))
+    assert np.array_equal(h, h2)
+    # zero field: h = 0
+    h0 = oracle.normalize(md, (np.zeros(md.nv), np.full(md.nv, oracle.ZERO_EXP, np.int32)))
+    assert np.all(h0 == 0)
+    del ex
+
+
+def test_normalize_tangent_unit_on_sphere():
+    m = meshgen.noisy_icosphere(3, 1)
+    md = oracle.mesh_data(m.V, m.F)
+    st = oracle.gs(md, oracle.bfs(md, [3]), oracle.diffusion_time(md), 50)
+    h = oracle.normalize(md, st)
+    P = m.V[m.F]
+    n = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    assert np.abs(np.einsum("ij,ij->i", h, n)).max() < 1e-12
+    assert np.allclose(np.linalg.norm(h, axis=1), 1.0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- face ADMM
+
+def test_face_admm_fixed_point_for_integrable_field():
+    m, md = _planar()
+    h = np.tile([0.6, 0.8, 0.0], (md.nf, 1))
+    g, y, lam, res = oracle.face_admm(md, h, 7)
+    assert np.allclose(g, h, atol=1e-15)
+    interior = md.edge_face[md.face_edge, 1] >= 0           # [nf, 3]
+    assert np.allclose(y[interior], np.broadcast_to(h[:, None, :], y.shape)[interior], atol=1e-15)
+    assert np.allclose(lam[interior], 0.0, atol=1e-13)
+    assert np.all(np.isnan(y[~interior]))
+
+
+@pytest.mark.parametrize("iters", [1, 2, 5])
+def test_face_admm_y_is_compatible(iters):
+    """After every Y-update the pair on each interior edge has equal
+    projections on the edge (eq. GradCompatibility holds for Y)."""
+    m = meshgen.noisy_icosphere(2, 8)
+    md = oracle.mesh_data(m.V, m.F)
+    o = oracle.solve(md, [0], "face", sweeps=40)
+    g, y, lam, res = oracle.face_admm(md, o["h"], iters)
+    ev = m.V[md.edges[:, 1]] - m.V[md.edges[:, 0]]
+    ev /= np.linalg.norm(ev, axis=1, keepdims=True)
+    y1 = y[md.edge_face[:, 0], md.edge_slot[:, 0]]
+    y2 = y[md.edge_face[:, 1], md.edge_slot[:, 1]]
+    assert np.abs(np.einsum("ij,ij->i", ev, y1 - y2)).max() < 1e-14
+
+
+@pytest.mark.parametrize("mesh,src", [(meshgen.jittered_grid(9, 4), 40), (meshgen.noisy_icosphere(2, 3), 0)])
+def test_face_admm_limit_is_poisson_solution(mesh, src):
+    """Run long, the face ADMM reaches the closest integrable field; its
+    integral is the least-squares Poisson solution of the original heat
+    method (Sec. 3.2) on these genus-0 meshes."""
+    md = oracle.mesh_data(mesh.V, mesh.F)
+    o = oracle.solve(md, [src], "face", sweeps=100)
+    g, y, lam, res = oracle.face_admm(md, o["h"], 6000)
+    d = oracle.integrate_face(md, o["bfs"], g)
+    phi = hm.poisson_face(md, o["h"], src)
+    assert np.abs(d - phi).max() < 1e-12
+    assert res[-1, 0] < 1e-12 and res[-1, 1] < 1e-10
+
+
+def test_face_admm_residuals_fall():
+    m = meshgen.noisy_icosphere(3, 8)
+    md = oracle.mesh_data(m.V, m.F)
+    o = oracle.solve(md, [0], "face", sweeps=60)
+    _, _, _, res = oracle.face_admm(md, o["h"], 40)
+    assert res[-1, 0] < 0.1 * res[0, 0] and res[-1, 1] < 0.1 * res[0, 1]
+    # |M|_F: square root of the face area summed over all interior-edge slots
+    assert np.allclose(res[:, 2], np.sqrt(np.sum(md.Af[md.edge_face[md.edge_face[:, 1] >= 0]])))
+
+
+# ---------------------------------------------------------------- edge ADMM
+
+def test_edge_admm_w_satisfies_face_condition():
+    m = meshgen.noisy_icosphere(2, 8)
+    md = oracle.mesh_data(m.V, m.F)
+    o = oracle.solve(md, [0], "edge", sweeps=40)
+    for iters in (1, 3, 10):
+        x, w, lam, z, res = oracle.edge_admm(md, o["h"], iters)
+        assert np.abs(np.sum(md.face_sign * w, axis=1)).max() < 1e-14
+
+
+def test_edge_admm_fixed_point_for_integrable_field():
+    m, md = _planar()
+    h = np.tile([0.6, 0.8, 0.0], (md.nf, 1))
+    x, w, lam, z, res = oracle.edge_admm(md, h, 5)
+    ev = m.V[md.edges[:, 1]] - m.V[md.edges[:, 0]]
+    assert np.allclose(x, ev @ h[0], atol=1e-15)
+    assert np.allclose(w, z, atol=1e-15) and np.allclose(lam, 0.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("mesh,src", [(meshgen.jittered_grid(9, 4), 40), (meshgen.noisy_icosphere(2, 3), 0)])
+def test_edge_admm_limit_is_least_squares(mesh, src):
+    md = oracle.mesh_data(mesh.V, mesh.F)
+    o = oracle.solve(md, [src], "edge", sweeps=100)
+    x, w, lam, z, res = oracle.edge_admm(md, o["h"], 6000)
+    d = oracle.integrate_edge(md, o["bfs"], x)
+    psi = hm.lsq_edge(md, z, src)
+    assert np.abs(d - psi).max() < 1e-12
+
+
+def test_edge_orientation_choice_is_invisible():
+    """The orientation halfedge of each edge may be either one (Sec. 4.1):
+    flipping some negates their x, z and lambda and leaves d unchanged."""
+    m = meshgen.noisy_icosphere(3, 2)
+    md = oracle.mesh_data(m.V, m.F)
+    flip = (meshgen.rng_for(9).random(md.ne) < 0.5).astype(np.uint8)
+    mdf = oracle.mesh_data(m.V, m.F, flip)
+    o = oracle.solve(md, [5], "edge", sweeps=60)
+    of = oracle.solve(mdf, [5], "edge", sweeps=60)
+    sgn = np.where(flip == 1, -1.0, 1.0)
+    assert np.allclose(of["x"], sgn * o["x"], rtol=0, atol=1e-15)
+    assert np.allclose(of["d"], o["d"], rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- integration
+
+def test_integration_exact_on_linear_fields():
+    """A gradient field of a linear function integrates exactly along any
+    breadth-first pairing (path independence, Sec. 3.3 and Sec. 4)."""
+    m, md = _planar(15, 2)
+    a = np.array([0.7, -0.2, 0.0])
+    src = 100
+    b = oracle.bfs(md, [src])
+    g = np.tile(a, (md.nf, 1))
+    exact = (m.V - m.V[src]) @ a
+    x = (m.V[md.edges[:, 1]] - m.V[md.edges[:, 0]]) @ a
+    # another valid pairing: the last neighbour in the previous set
+    alt = b.parent.copy()
+    for v in range(md.nv):
+        if b.level[v] > 0:
+            nb = md.col[md.rowptr[v]:md.rowptr[v + 1]]
+            alt[v] = nb[b.level[nb] == b.level[v] - 1].max()
+    for par in (None, alt):
+        assert np.allclose(oracle.integrate_face(md, b, g, par), exact, atol=1e-14)
+        assert np.allclose(oracle.integrate_edge(md, b, x, par), exact, atol=1e-14)
+
+
+def test_integration_sources_zero_unreachable_inf():
+    g = meshgen.jittered_grid(5, None)
+    V = np.concatenate([g.V, g.V + [2.0, 0, 0]])
+    F = np.concatenate([g.F, g.F + g.nv]).astype(np.int32)
+    md = oracle.mesh_data(V, F)
+    o = oracle.solve(md, [3, 20], "face", sweeps=20)
+    assert o["d"][3] == 0 and o["d"][20] == 0
+    assert np.all(np.isinf(o["d"][g.nv:])) and np.all(np.isfinite(o["d"][:g.nv]))
