@@ -1,0 +1,206 @@
+/*
+ * geoheat: geodesic distance on triangle meshes by the parallel heat method
+ * of Tao, Zhang, Deng, Fang, Peng and He, "Parallel and Scalable Heat
+ * Methods for Geodesic Distance Computation" (arXiv 1812.06060), on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The problem (Sec. 3): given a manifold triangle mesh M = (V, E, F), a set
+ * of source vertices and a diffusion time t, return the geodesic distance d
+ * from the source set at every vertex.  Algorithm 1: heat diffusion by
+ * breadth-first Gauss-Seidel (Sec. 3.1) -> face-wise normalised gradients
+ * h = -grad u / |grad u| -> an integrable gradient field by ADMM, face form
+ * (Sec. 3.2) or edge form (Sec. 4) -> breadth-first integration (Sec. 3.3).
+ *
+ * Conventions for every call:
+ *  - Every call returns a gh_status; outputs are written only on GH_OK.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it
+ *    passes.  Handles belong to the library until gh_mesh_free /
+ *    gh_ctx_destroy.
+ *  - Pointer arguments marked "host or device" may point to host memory or
+ *    to device memory of the context's GPU; the library tells them apart
+ *    with cudaPointerGetAttributes.  Other pointers are host pointers.
+ *  - All device work of a context runs on the context's stream (the legacy
+ *    default stream unless gh_ctx_set_stream set another one); blocking calls
+ *    synchronise that stream before they return.
+ *  - gh_last_error() returns a thread-local message for the last failing
+ *    call of the calling thread.
+ *  - Calls on one context must not run concurrently from several threads,
+ *    except gh_submit / gh_poll / gh_wait, which are thread-safe.
+ */
+#ifndef GEOHEAT_H
+#define GEOHEAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gh_ctx_s *gh_ctx;
+typedef struct gh_mesh_s *gh_mesh;
+typedef uint64_t gh_req;
+
+typedef enum {
+    GH_OK = 0,
+    GH_EINVAL = 1,        /* bad argument: null pointer, index out of range, empty source set, bad params */
+    GH_ENOMEM = 2,        /* device memory or the context's HBM budget is exhausted */
+    GH_EDEVICE = 3,       /* a CUDA call failed; see gh_last_error() */
+    GH_ETIMEOUT = 4,      /* a bounded wait ran out (a grid barrier inside a kernel, or gh_wait) */
+    GH_EBUSY = 5,         /* the request is not finished yet */
+    GH_ENOTFOUND = 6,     /* unknown request id */
+    GH_ENONMANIFOLD = 7   /* an edge in more than two faces, or two faces that cross an edge in the same direction */
+} gh_status;
+
+typedef enum { GH_FORM_FACE = 0, GH_FORM_EDGE = 1 } gh_form;
+
+/*
+ * Solver parameters (Sec. 3.1, Sec. 3.2, Sec. 4.1, Sec. 6).
+ *  m           diffusion-time factor: t = m * hbar^2, hbar = mean edge length
+ *              (eq. DiffusionTime); used when t <= 0.  Default 1.
+ *  t           explicit diffusion time when > 0.  Default 0.
+ *  gs_sweeps   outer Gauss-Seidel iterations of the diffusion step (Sec. 3.1).
+ *              Default 200.
+ *  admm_iters  ADMM iterations, I_max (Sec. 6).  Default 10.
+ *  mu          ADMM penalty parameter (Sec. 3.2, Sec. 4.1).  Default 100.
+ *  form        GH_FORM_FACE (Sec. 3.2 + eq. IntegrationStep) or GH_FORM_EDGE
+ *              (Sec. 4).  Default GH_FORM_EDGE.
+ *  fp64        0: sweeps and ADMM in FP32 (the default); 1: in FP64.
+ *              Geometry is always computed in FP64 and distances are always
+ *              accumulated in FP64.
+ *  diagnostics 1: also compute the heat residual E1 (eq. HeatSolutionError)
+ *              and the ADMM primal / dual residual norms of every iteration,
+ *              readable with gh_debug_dump.  Default 0.
+ */
+typedef struct {
+    double m;
+    double t;
+    int32_t gs_sweeps;
+    int32_t admm_iters;
+    double mu;
+    int32_t form;
+    int32_t fp64;
+    int32_t diagnostics;
+    int32_t reserved;
+} gh_params;
+
+/* Fills *p with the defaults listed above. */
+void gh_params_default(gh_params *p);
+
+/* Library version string. */
+const char *gh_version(void);
+
+/*
+ * Context on CUDA device `device`.  hbm_budget_bytes caps the device memory
+ * the context allocates (0: no cap beyond the device's).  The context owns
+ * its meshes.  Errors: GH_EINVAL (bad device), GH_EDEVICE.
+ */
+gh_status gh_ctx_create(int device, size_t hbm_budget_bytes, gh_ctx *out);
+gh_status gh_ctx_destroy(gh_ctx ctx);
+
+/* Stream for all device work of the context (a cudaStream_t, passed as a
+ * pointer; NULL = the legacy default stream).  The caller keeps the stream
+ * alive while the context uses it. */
+gh_status gh_ctx_set_stream(gh_ctx ctx, void *stream);
+
+/* Device bytes the context holds now. */
+gh_status gh_ctx_memory(gh_ctx ctx, size_t *bytes_in_use);
+
+/* Number of CUDA kernels the context has launched since it was created
+ * (every launch of every geoheat kernel, setup included). */
+gh_status gh_ctx_stats(gh_ctx ctx, uint64_t *kernel_launches);
+
+/*
+ * Mesh setup (the "initialization of data structures" of Sec. 6.4), done
+ * once per mesh on the device and kept resident for every later solve.
+ *  V  host or device, float64 [nv][3] vertex positions.
+ *  F  host or device, int32 [nf][3] faces, vertex indices, each face's loop
+ *     a->b->c->a consistently oriented over the mesh (an oriented 2-manifold,
+ *     Sec. 4.1), boundaries allowed.
+ * Builds the sorted one-ring of each vertex, edge ids (edges sorted by
+ * (min, max) vertex index), per-face edge ids and integrability signs
+ * s_k^f with orientation halfedges running from the smaller to the larger
+ * vertex index (eq. Integrability), vertex areas A_v (one third of the
+ * incident face area), cotangent weights theta_e = 1/2 sum cot(opposite
+ * angle) (Sec. 3.1), face gradient operators and the mean edge length.
+ * Errors: GH_EINVAL (nv < 3, nf < 1, an index outside [0, nv), a face with
+ * a repeated vertex), GH_ENONMANIFOLD, GH_ENOMEM, GH_EDEVICE.
+ */
+gh_status gh_mesh_load(gh_ctx ctx, const double *V, int64_t nv, const int32_t *F, int64_t nf, gh_mesh *out);
+
+/* Counts and mean edge length (hbar of eq. DiffusionTime).  Any output
+ * pointer may be NULL. */
+gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, double *mean_edge_len);
+
+gh_status gh_mesh_free(gh_mesh mesh);
+
+/*
+ * One geodesic distance field from one source set (Algorithm 1; Sec. 5.2 for
+ * several sources: all of them form D_0, u_0 = 1 on each, d = 0 on each).
+ *  src    host or device, int32 [nsrc] vertex indices; duplicates allowed.
+ *  d_out  host or device, float64 [nv]: distances; +infinity at vertices not
+ *         connected to any source.
+ * Errors: GH_EINVAL (nsrc < 1, a source outside [0, nv), bad params),
+ * GH_ENOMEM, GH_ETIMEOUT, GH_EDEVICE.
+ */
+gh_status gh_solve(gh_mesh mesh, const int32_t *src, int32_t nsrc, const gh_params *params, double *d_out);
+
+/*
+ * K independent source sets solved together as K right-hand sides of the
+ * same mesh, one persistent kernel per stage for all of them.
+ *  src_off  host, int32 [K+1]: set q is src[src_off[q] .. src_off[q+1]).
+ *  src      host, int32 [src_off[K]].
+ *  d_out    host or device, float64 [K][nv].
+ * Results are the same as K separate gh_solve calls.  Errors as gh_solve.
+ */
+gh_status gh_solve_batch(gh_mesh mesh, const int32_t *src_off, const int32_t *src, int32_t K,
+                         const gh_params *params, double *d_out);
+
+/*
+ * Intermediates of query `query` of the last gh_solve / gh_solve_batch on
+ * this mesh, copied to the host buffer `out`, for parity tests and
+ * diagnostics.  gh_debug_size gives the element count and element size in
+ * bytes of each item.
+ */
+typedef enum {
+    GH_DUMP_LEVEL = 0,      /* int32 [nv]  breadth-first set index i of each vertex (v in D_i), -1 unreachable */
+    GH_DUMP_PARENT = 1,     /* int32 [nv]  pairing vertex in D_{i-1} (first discoverer), -1 for sources/unreachable */
+    GH_DUMP_ORDER = 2,      /* int32 [nreach]  vertices in breadth-first (FIFO) order */
+    GH_DUMP_LEVEL_OFF = 3,  /* int32 [L+1] D_i = order[off[i] .. off[i+1]) */
+    GH_DUMP_U_MANT = 4,     /* float64 [nv] mantissa of u: u = mant * 2^exp */
+    GH_DUMP_U_EXP = 5,      /* int32 [nv]  binary exponent of u */
+    GH_DUMP_H = 6,          /* float64 [nf][3] normalised gradients h */
+    GH_DUMP_G = 7,          /* float64 [nf][3] face form: optimised gradients g */
+    GH_DUMP_X = 8,          /* float64 [ne]  edge form: optimised edge differences x */
+    GH_DUMP_D = 9,          /* float64 [nv]  distances */
+    GH_DUMP_EDGES = 10,     /* int32 [ne][2] (min, max) vertex pair of each edge */
+    GH_DUMP_FACE_EDGE = 11, /* int32 [nf][3] edge id of the edge opposite corner k */
+    GH_DUMP_FACE_SIGN = 12, /* int32 [nf][3] s_k^f in {-1, +1} */
+    GH_DUMP_THETA = 13,     /* float64 [ne]  cotangent weight per edge */
+    GH_DUMP_AV = 14,        /* float64 [nv]  vertex areas */
+    GH_DUMP_AF = 15,        /* float64 [nf]  face areas */
+    GH_DUMP_ROWPTR = 16,    /* int32 [nv+1]  one-ring CSR row pointers */
+    GH_DUMP_COL = 17,       /* int32 [2ne]   one-ring neighbours, ascending per row */
+    GH_DUMP_RESID = 18,     /* float64 [admm_iters][2] primal, dual residual norms (diagnostics = 1) */
+    GH_DUMP_E1 = 19,        /* float64 [1]   heat residual E1 (diagnostics = 1) */
+    GH_DUMP_T = 20          /* float64 [1]   diffusion time used */
+} gh_dump_item;
+
+gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *count, int32_t *elem_bytes);
+gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out);
+
+/* Per-stage device times of the last solve on this mesh, in milliseconds,
+ * measured with CUDA events on the context's stream, summed over the passes
+ * of a batch: ms6[0] breadth-first sets and layout, [1] Gauss-Seidel
+ * diffusion stage, [2] normalisation (and E1 with diagnostics), [3] ADMM,
+ * [4] integration, [5] the diffusion kernel launch alone. */
+gh_status gh_stage_times(gh_mesh mesh, double *ms6);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *gh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEOHEAT_H */

@@ -1,0 +1,539 @@
+// The C-ABI of include/geoheat.h: contexts, resident meshes, solves (single
+// and batched), intermediates for parity tests, error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct gh_ctx_s {
+    gh::Ctx c;
+    std::mutex mu;
+    std::vector<gh_mesh_s *> meshes;
+};
+
+struct gh_mesh_s {
+    gh_ctx_s *ctx = nullptr;
+    gh::MeshH h;
+};
+
+namespace gh {
+
+static thread_local std::string t_err;
+
+void set_error(const std::string &msg) { t_err = msg; }
+
+gh_status cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    if (e == cudaErrorMemoryAllocation) return GH_ENOMEM;
+    return GH_EDEVICE;
+}
+
+gh_status dalloc(Ctx *c, DBuf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return GH_OK;
+    dfree(c, b);
+    if (bytes == 0) bytes = 16;
+    if (c->budget && c->in_use + bytes > c->budget) {
+        set_error("device memory budget of the context exceeded (" + std::to_string(c->in_use + bytes) + " > " +
+                  std::to_string(c->budget) + " bytes)");
+        return GH_ENOMEM;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        (void)cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc");
+    }
+    b.bytes = bytes;
+    c->in_use += bytes;
+    return GH_OK;
+}
+
+void dfree(Ctx *c, DBuf &b) {
+    if (b.p) {
+        cudaFree(b.p);
+        c->in_use -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int *dev_status(Ctx *c) { return c->status_dev; }
+
+gh_status check_status(Ctx *c, const char *stage) {
+    GH_CUDA(cudaStreamSynchronize(c->stream));
+    GH_CUDA(cudaGetLastError());
+    int s = 0;
+    GH_CUDA(cudaMemcpy(&s, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s == DEV_OK) return GH_OK;
+    cudaMemset(c->status_dev, 0, sizeof(int));
+    switch (s) {
+    case DEV_EINVAL: set_error(std::string(stage) + ": invalid input (index out of range or repeated vertex in a face)"); return GH_EINVAL;
+    case DEV_ENONMANIFOLD: set_error(std::string(stage) + ": mesh is not an oriented 2-manifold"); return GH_ENONMANIFOLD;
+    case DEV_ETIMEOUT: set_error(std::string(stage) + ": a grid barrier wait ran out"); return GH_ETIMEOUT;
+    default: set_error(std::string(stage) + ": device error"); return GH_EDEVICE;
+    }
+}
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void free_ws(Ctx *c, QueryWs *w) {
+    DBuf *all[] = {&w->level, &w->parent, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->grow, &w->gent,
+                   &w->diag, &w->tiles, &w->ptile, &w->U0, &w->U1, &w->h, &w->g0, &w->g1, &w->l0, &w->l1, &w->z,
+                   &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1};
+    for (DBuf *b : all) dfree(c, *b);
+}
+
+// allocate (or keep) the workspace of one query for this mesh, precision and form
+static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int form, int iters) {
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    const size_t xs = fp64 ? sizeof(XVal<double>) : sizeof(XVal<float>);
+    const int64_t nv = m.nv, nf = m.nf, ne = m.ne, nnz = 2 * m.ne;
+    if (w.fp64 != fp64 || w.cap_nv != nv || w.cap_nf != nf || w.cap_ne != ne) {
+        free_ws(c, &w);
+        w.fp64 = fp64;
+        w.cap_nv = nv;
+        w.cap_nf = nf;
+        w.cap_ne = ne;
+        w.cap_nnz = nnz;
+    }
+    gh_status s;
+#define A(buf, bytes) if ((s = dalloc(c, w.buf, (size_t)(bytes))) != GH_OK) return s
+    A(level, 4 * nv); A(parent, 4 * nv); A(order, 4 * nv); A(pos, 4 * nv); A(key, 8 * nv);
+    A(lvl_off, 4 * (nv + 2)); A(meta, 16);
+    A(grow, 4 * (nv + 1)); A(gent, nnz * (4 + es)); A(diag, es * nv);
+    A(tiles, 8 * (nv + nv / TILE + 4)); A(ptile, 4 * (nv + 8));
+    A(U0, xs * nv); A(U1, xs * nv);
+    A(h, es * 3 * nf);
+    if (form == GH_FORM_FACE) {
+        A(g0, es * 3 * nf); A(g1, es * 3 * nf); A(l0, es * 9 * nf); A(l1, es * 9 * nf);
+    } else {
+        A(z, es * 3 * nf); A(w, es * 3 * nf); A(lam, es * 3 * nf); A(sz, es * ne); A(x, es * ne);
+    }
+    A(inc, 8 * nv); A(d0, 8 * nv); A(d1, 8 * nv); A(n0, 4 * (nv + 1)); A(n1, 4 * (nv + 1));
+    A(resid, 16 * std::max(iters, 1)); A(e1, 8);
+#undef A
+    return GH_OK;
+}
+
+static gh_status validate_params(const gh_params *p) {
+    if (!p) { set_error("params is NULL"); return GH_EINVAL; }
+    if (p->gs_sweeps < 1) { set_error("gs_sweeps must be >= 1"); return GH_EINVAL; }
+    if (p->admm_iters < 0) { set_error("admm_iters must be >= 0"); return GH_EINVAL; }
+    if (!(p->mu > 0)) { set_error("mu must be > 0"); return GH_EINVAL; }
+    if (p->form != GH_FORM_FACE && p->form != GH_FORM_EDGE) { set_error("form must be GH_FORM_FACE or GH_FORM_EDGE"); return GH_EINVAL; }
+    if (!(p->t > 0) && !(p->m > 0)) { set_error("either t > 0 or m > 0 is required"); return GH_EINVAL; }
+    return GH_OK;
+}
+
+// bytes one query's workspace needs
+static size_t ws_bytes(const DevMesh &m, int fp64, int form) {
+    const size_t es = fp64 ? 8 : 4, xs = fp64 ? 16 : 8;
+    size_t nv = m.nv, nf = m.nf, ne = m.ne;
+    size_t b = nv * (4 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (4 + es) + es * 3 * nf;
+    b += (form == GH_FORM_FACE) ? es * 24 * nf : es * (9 * nf + 2 * ne);
+    return b + (1 << 20);
+}
+
+// Run queries src[0..K) through the whole path; d_out (device) gets K x nv.
+static gh_status solve_impl(gh_mesh_s *mh, const std::vector<std::vector<int32_t>> &src, const gh_params *p,
+                            double *d_out_dev) {
+    Ctx *c = &mh->ctx->c;
+    DevMesh &m = mh->h.m;
+    const int K = (int)src.size();
+    const double t = (p->t > 0) ? p->t : p->m * m.hbar * m.hbar;
+    // queries per pass: as many as the budget (or 80% of free memory) allows, at most 64
+    size_t per = ws_bytes(m, p->fp64, p->form);
+    size_t avail;
+    if (c->budget) {
+        avail = c->budget > c->in_use ? c->budget - c->in_use : 0;
+    } else {
+        size_t fr = 0, tot = 0;
+        GH_CUDA(cudaMemGetInfo(&fr, &tot));
+        avail = (size_t)(0.8 * (double)fr);
+    }
+    for (QueryWs *w : mh->h.ws) avail += w->level.p ? per : 0;  // workspaces already held are reusable
+    int chunk = (int)std::min<size_t>(64, std::max<size_t>(1, avail / per));
+    chunk = std::min(chunk, K);
+    while ((int)mh->h.ws.size() < chunk) mh->h.ws.push_back(new QueryWs());
+    cudaEvent_t ev[8];
+    for (auto &e : ev) GH_CUDA(cudaEventCreate(&e));
+    double ms[5] = {0, 0, 0, 0, 0}, gs_ms = 0.0;
+    gh_status s = GH_OK;
+    for (int q0 = 0; q0 < K && s == GH_OK; q0 += chunk) {
+        int kq = std::min(chunk, K - q0);
+        std::vector<QueryWs *> ws(mh->h.ws.begin(), mh->h.ws.begin() + kq);
+        for (int q = 0; q < kq && s == GH_OK; ++q) {
+            s = ensure_ws(c, m, *ws[q], p->fp64, p->form, p->admm_iters);
+            ws[q]->diagnostics = p->diagnostics;
+        }
+        if (s != GH_OK) break;
+        std::vector<std::vector<int32_t>> part(src.begin() + q0, src.begin() + q0 + kq);
+        cudaEventRecord(ev[0], c->stream);
+        if ((s = run_bfs(c, m, ws, part)) != GH_OK) break;
+        for (int q = 0; q < kq && s == GH_OK; ++q) s = build_layout(c, m, *ws[q], t);
+        if (s != GH_OK) break;
+        cudaEventRecord(ev[1], c->stream);
+        if ((s = run_gs(c, m, ws, p->gs_sweeps, ev[6], ev[7])) != GH_OK) break;
+        cudaEventRecord(ev[2], c->stream);
+        if ((s = check_status(c, "diffusion")) != GH_OK) break;
+        for (int q = 0; q < kq && s == GH_OK; ++q) {
+            if (p->diagnostics) s = run_heat_residual(c, m, *ws[q]);
+            if (s == GH_OK) s = run_normalize(c, m, *ws[q]);
+        }
+        cudaEventRecord(ev[3], c->stream);
+        for (int q = 0; q < kq && s == GH_OK; ++q) {
+            s = (p->form == GH_FORM_FACE) ? run_face_admm(c, m, *ws[q], p->admm_iters, p->mu)
+                                          : run_edge_admm(c, m, *ws[q], p->admm_iters, p->mu);
+        }
+        cudaEventRecord(ev[4], c->stream);
+        for (int q = 0; q < kq && s == GH_OK; ++q)
+            s = run_integrate(c, m, *ws[q], d_out_dev ? d_out_dev + (size_t)(q0 + q) * m.nv : nullptr);
+        cudaEventRecord(ev[5], c->stream);
+        if (s != GH_OK) break;
+        if ((s = check_status(c, "solve")) != GH_OK) break;
+        for (int i = 0; i < 5; ++i) {
+            float x = 0;
+            cudaEventElapsedTime(&x, ev[i], ev[i + 1]);
+            ms[i] += x;
+        }
+        float xg = 0;
+        cudaEventElapsedTime(&xg, ev[6], ev[7]);
+        gs_ms += xg;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (s == GH_OK) {
+        mh->h.last_k = std::min(K, chunk);
+        std::copy(ms, ms + 5, mh->h.stage_ms);
+        mh->h.gs_kernel_ms = gs_ms;
+    }
+    return s;
+}
+
+// sources of one set, validated, sorted and de-duplicated
+static gh_status prep_sources(const int32_t *src, int32_t nsrc, int64_t nv, std::vector<int32_t> &out) {
+    if (!src || nsrc < 1) { set_error("a source set needs at least one vertex"); return GH_EINVAL; }
+    out.resize(nsrc);
+    if (is_device_ptr(src)) {
+        GH_CUDA(cudaMemcpy(out.data(), src, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(out.data(), src, sizeof(int32_t) * nsrc);
+    }
+    for (int32_t v : out)
+        if (v < 0 || v >= nv) { set_error("source vertex " + std::to_string(v) + " outside [0, nv)"); return GH_EINVAL; }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return GH_OK;
+}
+
+static gh_status solve_to(gh_mesh_s *mh, const std::vector<std::vector<int32_t>> &sets, const gh_params *p,
+                          double *d_out) {
+    Ctx *c = &mh->ctx->c;
+    const size_t bytes = sizeof(double) * (size_t)mh->h.m.nv * sets.size();
+    if (is_device_ptr(d_out)) return solve_impl(mh, sets, p, d_out);
+    double *tmp = nullptr;
+    GH_CUDA(cudaMallocAsync((void **)&tmp, bytes, c->stream));
+    gh_status s = solve_impl(mh, sets, p, tmp);
+    if (s == GH_OK) {
+        cudaError_t e = cudaMemcpyAsync(d_out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) s = cuda_fail(e, "copy of the distances to the host");
+    }
+    cudaFreeAsync(tmp, c->stream);
+    return s;
+}
+
+}  // namespace gh
+
+using namespace gh;
+
+extern "C" {
+
+void gh_params_default(gh_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->m = 1.0;
+    p->t = 0.0;
+    p->gs_sweeps = 200;
+    p->admm_iters = 10;
+    p->mu = 100.0;
+    p->form = GH_FORM_EDGE;
+    p->fp64 = 0;
+    p->diagnostics = 0;
+}
+
+const char *gh_version(void) { return "geoheat 0.1 (sm_103a)"; }
+
+const char *gh_last_error(void) { return t_err.c_str(); }
+
+gh_status gh_ctx_create(int device, size_t hbm_budget_bytes, gh_ctx *out) {
+    if (!out) { set_error("out is NULL"); return GH_EINVAL; }
+    int n = 0;
+    GH_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) { set_error("no such CUDA device"); return GH_EINVAL; }
+    GH_CUDA(cudaSetDevice(device));
+    auto *c = new gh_ctx_s();
+    c->c.device = device;
+    c->c.budget = hbm_budget_bytes;
+    cudaError_t e = cudaDeviceGetAttribute(&c->c.num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->c.status_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->c.status_dev, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->c.bar_dev, sizeof(GridBarrier));
+    if (e == cudaSuccess) e = cudaMemset(c->c.bar_dev, 0, sizeof(GridBarrier));
+    if (e != cudaSuccess) {
+        if (c->c.status_dev) cudaFree(c->c.status_dev);
+        if (c->c.bar_dev) cudaFree(c->c.bar_dev);
+        delete c;
+        return cuda_fail(e, "context setup");
+    }
+    *out = c;
+    return GH_OK;
+}
+
+gh_status gh_mesh_free(gh_mesh mesh);
+
+gh_status gh_ctx_destroy(gh_ctx ctx) {
+    if (!ctx) return GH_EINVAL;
+    std::vector<gh_mesh_s *> ms = ctx->meshes;
+    for (gh_mesh_s *m : ms) gh_mesh_free(m);
+    cudaFree(ctx->c.status_dev);
+    cudaFree(ctx->c.bar_dev);
+    delete ctx;
+    return GH_OK;
+}
+
+gh_status gh_ctx_set_stream(gh_ctx ctx, void *stream) {
+    if (!ctx) { set_error("ctx is NULL"); return GH_EINVAL; }
+    ctx->c.stream = static_cast<cudaStream_t>(stream);
+    return GH_OK;
+}
+
+gh_status gh_ctx_memory(gh_ctx ctx, size_t *bytes) {
+    if (!ctx || !bytes) { set_error("NULL argument"); return GH_EINVAL; }
+    *bytes = ctx->c.in_use;
+    return GH_OK;
+}
+
+gh_status gh_ctx_stats(gh_ctx ctx, uint64_t *kernel_launches) {
+    if (!ctx || !kernel_launches) { set_error("NULL argument"); return GH_EINVAL; }
+    *kernel_launches = ctx->c.launches;
+    return GH_OK;
+}
+
+gh_status gh_mesh_load(gh_ctx ctx, const double *V, int64_t nv, const int32_t *F, int64_t nf, gh_mesh *out) {
+    if (!ctx || !V || !F || !out) { set_error("NULL argument"); return GH_EINVAL; }
+    if (nv < 3 || nf < 1) { set_error("a mesh needs nv >= 3 and nf >= 1"); return GH_EINVAL; }
+    if (6 * nf >= (int64_t)INT32_MAX || nv >= (int64_t)INT32_MAX / 2) { set_error("mesh too large for 32-bit indices"); return GH_EINVAL; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    GH_CUDA(cudaSetDevice(ctx->c.device));
+    auto *mh = new gh_mesh_s();
+    mh->ctx = ctx;
+    mh->h.ctx = &ctx->c;
+    mh->h.m.nv = nv;
+    mh->h.m.nf = nf;
+    gh_status s = build_mesh(&ctx->c, mh->h.m, V, F);
+    if (s != GH_OK) {
+        DevMesh &m = mh->h.m;
+        DBuf *all[] = {&m.P, &m.F, &m.rowptr, &m.col, &m.col_edge, &m.edges, &m.face_edge, &m.face_sign, &m.edge_face,
+                       &m.edge_slot, &m.twin, &m.Af, &m.Av, &m.theta, &m.ev, &m.gradop, &m.Aff};
+        for (DBuf *b : all) dfree(&ctx->c, *b);
+        delete mh;
+        return s;
+    }
+    ctx->meshes.push_back(mh);
+    *out = mh;
+    return GH_OK;
+}
+
+gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, double *hbar) {
+    if (!mesh) { set_error("mesh is NULL"); return GH_EINVAL; }
+    if (nv) *nv = mesh->h.m.nv;
+    if (ne) *ne = mesh->h.m.ne;
+    if (nf) *nf = mesh->h.m.nf;
+    if (hbar) *hbar = mesh->h.m.hbar;
+    return GH_OK;
+}
+
+gh_status gh_mesh_free(gh_mesh mesh) {
+    if (!mesh) return GH_EINVAL;
+    gh_ctx_s *ctx = mesh->ctx;
+    Ctx *c = &ctx->c;
+    cudaStreamSynchronize(c->stream);
+    for (QueryWs *w : mesh->h.ws) {
+        free_ws(c, w);
+        delete w;
+    }
+    DevMesh &m = mesh->h.m;
+    DBuf *all[] = {&m.P, &m.F, &m.rowptr, &m.col, &m.col_edge, &m.edges, &m.face_edge, &m.face_sign, &m.edge_face,
+                   &m.edge_slot, &m.twin, &m.Af, &m.Av, &m.theta, &m.ev, &m.gradop, &m.Aff};
+    for (DBuf *b : all) dfree(c, *b);
+    auto it = std::find(ctx->meshes.begin(), ctx->meshes.end(), mesh);
+    if (it != ctx->meshes.end()) ctx->meshes.erase(it);
+    delete mesh;
+    return GH_OK;
+}
+
+gh_status gh_solve(gh_mesh mesh, const int32_t *src, int32_t nsrc, const gh_params *params, double *d_out) {
+    if (!mesh || !d_out) { set_error("NULL argument"); return GH_EINVAL; }
+    gh_status s = validate_params(params);
+    if (s != GH_OK) return s;
+    std::lock_guard<std::mutex> lk(mesh->ctx->mu);
+    GH_CUDA(cudaSetDevice(mesh->ctx->c.device));
+    std::vector<std::vector<int32_t>> sets(1);
+    if ((s = prep_sources(src, nsrc, mesh->h.m.nv, sets[0])) != GH_OK) return s;
+    return solve_to(mesh, sets, params, d_out);
+}
+
+gh_status gh_solve_batch(gh_mesh mesh, const int32_t *src_off, const int32_t *src, int32_t K, const gh_params *params,
+                         double *d_out) {
+    if (!mesh || !src_off || !src || !d_out || K < 1) { set_error("NULL argument or K < 1"); return GH_EINVAL; }
+    gh_status s = validate_params(params);
+    if (s != GH_OK) return s;
+    std::lock_guard<std::mutex> lk(mesh->ctx->mu);
+    GH_CUDA(cudaSetDevice(mesh->ctx->c.device));
+    std::vector<std::vector<int32_t>> sets(K);
+    for (int q = 0; q < K; ++q) {
+        int32_t b = src_off[q], e = src_off[q + 1];
+        if (b < 0 || e <= b) { set_error("src_off must be increasing and start at >= 0"); return GH_EINVAL; }
+        if ((s = prep_sources(src + b, e - b, mesh->h.m.nv, sets[q])) != GH_OK) return s;
+    }
+    return solve_to(mesh, sets, params, d_out);
+}
+
+gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *count, int32_t *elem_bytes) {
+    if (!mesh || !count || !elem_bytes) { set_error("NULL argument"); return GH_EINVAL; }
+    const DevMesh &m = mesh->h.m;
+    QueryWs *w = (query >= 0 && query < (int)mesh->h.ws.size()) ? mesh->h.ws[query] : nullptr;
+    bool need_q = !(what == GH_DUMP_EDGES || what == GH_DUMP_FACE_EDGE || what == GH_DUMP_FACE_SIGN ||
+                    what == GH_DUMP_THETA || what == GH_DUMP_AV || what == GH_DUMP_AF || what == GH_DUMP_ROWPTR ||
+                    what == GH_DUMP_COL);
+    if (need_q && (!w || !w->level.p)) { set_error("no such query in the last solve"); return GH_EINVAL; }
+    int64_t n = 0;
+    int32_t eb = 4;
+    switch (what) {
+    case GH_DUMP_LEVEL: case GH_DUMP_PARENT: n = m.nv; break;
+    case GH_DUMP_ORDER: n = w->nreach; break;
+    case GH_DUMP_LEVEL_OFF: n = w->nlev + 1; break;
+    case GH_DUMP_U_MANT: n = m.nv; eb = 8; break;
+    case GH_DUMP_U_EXP: n = m.nv; break;
+    case GH_DUMP_H: n = 3 * m.nf; eb = 8; break;
+    case GH_DUMP_G: if (w->form != GH_FORM_FACE) { set_error("last solve was not in the face form"); return GH_EINVAL; }
+        n = 3 * m.nf; eb = 8; break;
+    case GH_DUMP_X: if (w->form != GH_FORM_EDGE) { set_error("last solve was not in the edge form"); return GH_EINVAL; }
+        n = m.ne; eb = 8; break;
+    case GH_DUMP_D: n = m.nv; eb = 8; break;
+    case GH_DUMP_EDGES: n = 2 * m.ne; break;
+    case GH_DUMP_FACE_EDGE: case GH_DUMP_FACE_SIGN: n = 3 * m.nf; break;
+    case GH_DUMP_THETA: n = m.ne; eb = 8; break;
+    case GH_DUMP_AV: n = m.nv; eb = 8; break;
+    case GH_DUMP_AF: n = m.nf; eb = 8; break;
+    case GH_DUMP_ROWPTR: n = m.nv + 1; break;
+    case GH_DUMP_COL: n = 2 * m.ne; break;
+    case GH_DUMP_RESID: if (!w->diagnostics) { set_error("solve ran without diagnostics"); return GH_EINVAL; }
+        n = 2 * w->admm_iters; eb = 8; break;
+    case GH_DUMP_E1: if (!w->diagnostics) { set_error("solve ran without diagnostics"); return GH_EINVAL; }
+        n = 1; eb = 8; break;
+    case GH_DUMP_T: n = 1; eb = 8; break;
+    default: set_error("unknown dump item"); return GH_EINVAL;
+    }
+    *count = n;
+    *elem_bytes = eb;
+    return GH_OK;
+}
+
+static gh_status copy_real(const void *dev, int fp64, int64_t n, double *out) {
+    if (fp64) {
+        GH_CUDA(cudaMemcpy(out, dev, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> tmp(n);
+        GH_CUDA(cudaMemcpy(tmp.data(), dev, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) out[i] = tmp[i];
+    }
+    return GH_OK;
+}
+
+gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out) {
+    int64_t n = 0;
+    int32_t eb = 0;
+    gh_status s = gh_debug_size(mesh, query, what, &n, &eb);
+    if (s != GH_OK) return s;
+    if (!out) { set_error("out is NULL"); return GH_EINVAL; }
+    std::lock_guard<std::mutex> lk(mesh->ctx->mu);
+    Ctx *c = &mesh->ctx->c;
+    GH_CUDA(cudaStreamSynchronize(c->stream));
+    const DevMesh &m = mesh->h.m;
+    QueryWs *w = (query >= 0 && query < (int)mesh->h.ws.size()) ? mesh->h.ws[query] : nullptr;
+    auto cp = [&](const DBuf &b, size_t bytes) -> gh_status {
+        GH_CUDA(cudaMemcpy(out, b.p, bytes, cudaMemcpyDeviceToHost));
+        return GH_OK;
+    };
+    switch (what) {
+    case GH_DUMP_LEVEL: return cp(w->level, 4 * n);
+    case GH_DUMP_PARENT: return cp(w->parent, 4 * n);
+    case GH_DUMP_ORDER: return cp(w->order, 4 * n);
+    case GH_DUMP_LEVEL_OFF: return cp(w->lvl_off, 4 * n);
+    case GH_DUMP_U_MANT:
+    case GH_DUMP_U_EXP: {
+        // state is in queue order; scatter back to vertex order
+        std::vector<int32_t> pos(m.nv);
+        GH_CUDA(cudaMemcpy(pos.data(), w->pos.p, 4 * m.nv, cudaMemcpyDeviceToHost));
+        const DBuf &U = w->final_buf ? w->U1 : w->U0;
+        std::vector<double> mant(m.nv, 0.0);
+        std::vector<int32_t> ex(m.nv, kZeroExp);
+        if (w->fp64) {
+            std::vector<XVal<double>> u(w->nreach);
+            GH_CUDA(cudaMemcpy(u.data(), U.p, sizeof(XVal<double>) * w->nreach, cudaMemcpyDeviceToHost));
+            for (int64_t v = 0; v < m.nv; ++v) if (pos[v] >= 0) { mant[v] = u[pos[v]].m; ex[v] = u[pos[v]].e; }
+        } else {
+            std::vector<XVal<float>> u(w->nreach);
+            GH_CUDA(cudaMemcpy(u.data(), U.p, sizeof(XVal<float>) * w->nreach, cudaMemcpyDeviceToHost));
+            for (int64_t v = 0; v < m.nv; ++v) if (pos[v] >= 0) { mant[v] = u[pos[v]].m; ex[v] = u[pos[v]].e; }
+        }
+        if (what == GH_DUMP_U_MANT) std::memcpy(out, mant.data(), 8 * m.nv);
+        else std::memcpy(out, ex.data(), 4 * m.nv);
+        return GH_OK;
+    }
+    case GH_DUMP_H: return copy_real(w->h.p, w->fp64, n, (double *)out);
+    case GH_DUMP_G: return copy_real(w->g0.p, w->fp64, n, (double *)out);
+    case GH_DUMP_X: return copy_real(w->x.p, w->fp64, n, (double *)out);
+    case GH_DUMP_D: return cp(w->d0, 8 * n);
+    case GH_DUMP_EDGES: return cp(m.edges, 4 * n);
+    case GH_DUMP_FACE_EDGE: return cp(m.face_edge, 4 * n);
+    case GH_DUMP_FACE_SIGN: {
+        std::vector<int8_t> sg(n);
+        GH_CUDA(cudaMemcpy(sg.data(), m.face_sign.p, n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) ((int32_t *)out)[i] = sg[i];
+        return GH_OK;
+    }
+    case GH_DUMP_THETA: return cp(m.theta, 8 * n);
+    case GH_DUMP_AV: return cp(m.Av, 8 * n);
+    case GH_DUMP_AF: return cp(m.Af, 8 * n);
+    case GH_DUMP_ROWPTR: return cp(m.rowptr, 4 * n);
+    case GH_DUMP_COL: return cp(m.col, 4 * n);
+    case GH_DUMP_RESID: return cp(w->resid, 8 * n);
+    case GH_DUMP_E1: return cp(w->e1, 8);
+    case GH_DUMP_T: std::memcpy(out, &w->t, 8); return GH_OK;
+    default: set_error("unknown dump item"); return GH_EINVAL;
+    }
+}
+
+gh_status gh_stage_times(gh_mesh mesh, double *ms6) {
+    if (!mesh || !ms6) { set_error("NULL argument"); return GH_EINVAL; }
+    std::copy(mesh->h.stage_ms, mesh->h.stage_ms + 5, ms6);
+    ms6[5] = mesh->h.gs_kernel_ms;
+    return GH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Breadth-first vertex sets and pairing (eq. VertexSets, Sec. 3.3, Sec. 5.2)
+// and the per-query level-ordered layout the Gauss-Seidel kernel streams.
+//
+// The traversal reproduces a FIFO queue exactly: D_0 is the sorted source
+// set; the rank of a vertex is its position in the queue; a vertex of D_{i+1}
+// is discovered by its neighbour in D_i of lowest rank (the first one popped)
+// and sits in the queue ordered by (rank of that parent, position in the
+// parent's ascending one-ring).  Per set: every parent offers the key
+// (rank << 32 | slot) to each undiscovered neighbour with a 64-bit atomicMin;
+// a parent then counts the neighbours whose key is its own, an exclusive scan
+// over the parents in rank order gives each parent's first child position.
+// One CTA walks all sets of one query (one CTA per query of a batch).
+#include "internal.cuh"
+
+namespace gh {
+
+namespace {
+
+constexpr int BT = 1024;
+
+struct BfsArgs {
+    const int32_t *rowptr;
+    const int32_t *col;
+    int32_t *level;
+    int32_t *parent;
+    int32_t *order;
+    unsigned long long *key;
+    int32_t *lvl_off;
+    int32_t *meta;
+    int32_t n0;
+};
+
+__device__ int32_t bt_scan(int32_t v, int32_t &excl) {
+    __shared__ int32_t ws[BT / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t s = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    excl = (wid ? ws[wid - 1] : 0) + x - v;
+    int32_t total = ws[BT / 32 - 1];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
+    const BfsArgs a = all[blockIdx.x];
+    int lo = 0, hi = a.n0, nlev = 1;
+    if (threadIdx.x == 0) a.lvl_off[0] = 0;
+    while (true) {
+        // every parent offers its key to its undiscovered neighbours
+        for (int r = lo + threadIdx.x; r < hi; r += BT) {
+            int p = __ldcg(&a.order[r]);
+            int b = a.rowptr[p], e = a.rowptr[p + 1];
+            for (int j = b; j < e; ++j) {
+                int w = a.col[j];
+                if (__ldcg(&a.level[w]) < 0)
+                    atomicMin(&a.key[w], ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b));
+            }
+        }
+        __syncthreads();
+        // children in (parent rank, slot) order
+        int base = hi;
+        for (int c0 = lo; c0 < hi; c0 += BT) {
+            int r = c0 + threadIdx.x;
+            int cnt = 0, p = -1, b = 0, e = 0;
+            if (r < hi) {
+                p = __ldcg(&a.order[r]);
+                b = a.rowptr[p];
+                e = a.rowptr[p + 1];
+                for (int j = b; j < e; ++j) {
+                    unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
+                    if (__ldcg(&a.key[a.col[j]]) == mine) ++cnt;
+                }
+            }
+            int excl;
+            int total = bt_scan(cnt, excl);
+            if (cnt) {
+                int at = base + excl;
+                for (int j = b; j < e; ++j) {
+                    int w = a.col[j];
+                    unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
+                    if (__ldcg(&a.key[w]) == mine) {
+                        a.order[at++] = w;
+                        a.level[w] = nlev;
+                        a.parent[w] = p;
+                    }
+                }
+            }
+            base += total;
+        }
+        __syncthreads();
+        if (base == hi) break;
+        if (threadIdx.x == 0) a.lvl_off[nlev] = hi;
+        ++nlev;
+        lo = hi;
+        hi = base;
+    }
+    if (threadIdx.x == 0) {
+        a.lvl_off[nlev] = hi;
+        a.meta[0] = nlev;
+        a.meta[1] = hi;
+    }
+}
+
+__global__ void k_seed(int32_t *level, const int32_t *order, int n0) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n0) level[order[i]] = 0;
+}
+
+__global__ void k_pos(const int32_t *__restrict__ order, int n, int32_t *pos) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) pos[order[r]] = r;
+}
+
+__global__ void k_row_len(const int32_t *__restrict__ order, int n, const int32_t *__restrict__ rowptr, int32_t *len) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) {
+        int v = order[r];
+        len[r] = rowptr[v + 1] - rowptr[v];
+    }
+}
+
+// row r of the level-ordered layout: neighbours renumbered to queue positions
+// with weight t*theta; diag = A_v + t * sum theta (FP64, then rounded)
+template <class T>
+__global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const int32_t *__restrict__ rowptr,
+                              const int32_t *__restrict__ col, const int32_t *__restrict__ col_edge,
+                              const double *__restrict__ theta, const double *__restrict__ Av,
+                              const int32_t *__restrict__ pos, const int32_t *__restrict__ grow, double t,
+                              int32_t *gcol, T *gw, T *diag) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int v = order[r];
+    int b = rowptr[v], e = rowptr[v + 1], o = grow[r];
+    double sum = 0.0;
+    for (int j = b; j < e; ++j) {
+        double th = theta[col_edge[j]];
+        sum += th;
+        gcol[o + (j - b)] = pos[col[j]];
+        gw[o + (j - b)] = (T)(t * th);
+    }
+    diag[r] = (T)(Av[v] + t * sum);
+}
+
+// tiles of at most TILE queue positions inside one set, listed set by set,
+// even sets first, then odd sets; ptile holds, per parity, the running tile
+// count before each set of that parity
+__global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_off, int nlev, int32_t *ptile,
+                                              int2 *tiles) {
+    int n_even = (nlev + 1) / 2, n_odd = nlev / 2;
+    int32_t *p0 = ptile, *p1 = ptile + n_even + 1;
+    for (int par = 0; par < 2; ++par) {
+        int nl = par ? n_odd : n_even;
+        int32_t *pp = par ? p1 : p0;
+        int carry = 0;
+        for (int c0 = 0; c0 < nl; c0 += BT) {
+            int j = c0 + threadIdx.x;
+            int cnt = 0;
+            if (j < nl) {
+                int i = par + 2 * j;
+                int sz = lvl_off[i + 1] - lvl_off[i];
+                cnt = (sz + TILE - 1) / TILE;
+            }
+            int excl;
+            int tot = bt_scan(cnt, excl);
+            if (j < nl) pp[j] = carry + excl;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) pp[nl] = carry;
+        __syncthreads();
+    }
+    int base1 = p0[n_even];
+    for (int i = threadIdx.x; i < nlev; i += BT) {
+        int par = i & 1, j = i >> 1;
+        int first = (par ? base1 + p1[j] : p0[j]);
+        int s = lvl_off[i], e = lvl_off[i + 1];
+        for (int k = 0; s + k * TILE < e; ++k) tiles[first + k] = make_int2(i, s + k * TILE);
+    }
+}
+
+}  // namespace
+
+gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src) {
+    cudaStream_t st = c->stream;
+    int K = (int)src.size();
+    std::vector<BfsArgs> args(K);
+    for (int q = 0; q < K; ++q) {
+        QueryWs &w = *ws[q];
+        GH_CUDA(cudaMemsetAsync(w.level.p, 0xff, sizeof(int32_t) * m.nv, st));
+        GH_CUDA(cudaMemsetAsync(w.parent.p, 0xff, sizeof(int32_t) * m.nv, st));
+        GH_CUDA(cudaMemsetAsync(w.key.p, 0xff, sizeof(unsigned long long) * m.nv, st));
+        GH_CUDA(cudaMemcpyAsync(w.order.p, src[q].data(), sizeof(int32_t) * src[q].size(), cudaMemcpyHostToDevice, st));
+        k_seed<<<blocks_for((int64_t)src[q].size(), 256), 256, 0, st>>>(ptr<int32_t>(w.level), ptr<int32_t>(w.order),
+                                                                       (int)src[q].size()); ++c->launches;
+        args[q] = BfsArgs{ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(w.level), ptr<int32_t>(w.parent),
+                          ptr<int32_t>(w.order), ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off),
+                          ptr<int32_t>(w.meta), (int32_t)src[q].size()};
+    }
+    BfsArgs *dargs = nullptr;
+    GH_CUDA(cudaMallocAsync((void **)&dargs, sizeof(BfsArgs) * K, st));
+    GH_CUDA(cudaMemcpyAsync(dargs, args.data(), sizeof(BfsArgs) * K, cudaMemcpyHostToDevice, st));
+    k_bfs<<<K, BT, 0, st>>>(dargs); ++c->launches;
+    cudaError_t le = cudaGetLastError();
+    cudaFreeAsync(dargs, st);
+    if (le != cudaSuccess) return cuda_fail(le, "k_bfs");
+    std::vector<int32_t> meta(2 * K);
+    for (int q = 0; q < K; ++q)
+        GH_CUDA(cudaMemcpyAsync(&meta[2 * q], ws[q]->meta.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GH_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < K; ++q) {
+        ws[q]->nlev = meta[2 * q];
+        ws[q]->nreach = meta[2 * q + 1];
+    }
+    return GH_OK;
+}
+
+gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
+    cudaStream_t st = c->stream;
+    int n = q.nreach;
+    GH_CUDA(cudaMemsetAsync(q.pos.p, 0xff, sizeof(int32_t) * m.nv, st));
+    k_pos<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(q.pos)); ++c->launches;
+    int32_t *len = ptr<int32_t>(q.n0);
+    k_row_len<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), len); ++c->launches;
+    gh_status s = exclusive_scan_u32_dev(c, len, ptr<int32_t>(q.grow), n);
+    if (s != GH_OK) return s;
+    int32_t *gcol = ptr<int32_t>(q.gent);
+    if (q.fp64) {
+        double *gw = reinterpret_cast<double *>(gcol + q.cap_nnz);
+        k_fill_layout<double><<<blocks_for(n, 256), 256, 0, st>>>(
+            ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
+            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t, gcol, gw,
+            ptr<double>(q.diag)); ++c->launches;
+    } else {
+        float *gw = reinterpret_cast<float *>(gcol + q.cap_nnz);
+        k_fill_layout<float><<<blocks_for(n, 256), 256, 0, st>>>(
+            ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
+            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t, gcol, gw,
+            ptr<float>(q.diag)); ++c->launches;
+    }
+    k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.ptile), ptr<int2>(q.tiles)); ++c->launches;
+    GH_CUDA(cudaGetLastError());
+    q.t = t;
+    return GH_OK;
+}
+
+}  // namespace gh

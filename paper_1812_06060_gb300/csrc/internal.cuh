@@ -1,0 +1,175 @@
+// Internal declarations of the geoheat CUDA library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/geoheat.h"
+
+namespace gh {
+
+// ---------------------------------------------------------------- errors
+
+// device-side error codes written to a status word by kernels
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_EINVAL = 1,
+    DEV_ENONMANIFOLD = 2,
+    DEV_ETIMEOUT = 3,
+};
+
+void set_error(const std::string &msg);
+gh_status cuda_fail(cudaError_t e, const char *what);
+
+#define GH_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return ::gh::cuda_fail(_e, #call);      \
+    } while (0)
+
+// ---------------------------------------------------------------- memory
+
+struct Ctx;
+
+// device allocation charged to the context's budget
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+gh_status dalloc(Ctx *c, DBuf &b, size_t bytes);
+void dfree(Ctx *c, DBuf &b);
+
+template <class X>
+inline X *ptr(const DBuf &b) { return static_cast<X *>(b.p); }
+
+// ---------------------------------------------------------------- the extended value
+
+// A heat value u = m * 2^e.  The heat solution falls by about e^-1 per edge
+// length away from the sources; on large meshes it spans more binary
+// exponents than any IEEE format holds, so the exponent travels separately.
+// m == 0 encodes 0 and then e == kZeroExp.
+constexpr int kZeroExp = -(1 << 28);
+
+template <class T> struct alignas(sizeof(T) == 4 ? 8 : 16) XVal {
+    T m;
+    int e;
+};
+
+// ---------------------------------------------------------------- mesh
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int abort;
+    int pad;
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;     // 0: unlimited
+    size_t in_use = 0;
+    int num_sms = 0;
+    int *status_dev = nullptr;       // device status word written by kernels
+    GridBarrier *bar_dev = nullptr;  // grid barrier of the persistent kernels
+    unsigned long long launches = 0; // kernels launched by this context so far
+};
+
+// Resident per-mesh operators (built once by gh_mesh_load).
+struct DevMesh {
+    int64_t nv = 0, nf = 0, ne = 0;
+    double hbar = 0.0;
+    DBuf P;          // double [nv*3]
+    DBuf F;          // int32 [nf*3]
+    DBuf rowptr;     // int32 [nv+1]
+    DBuf col;        // int32 [2ne] neighbours ascending
+    DBuf col_edge;   // int32 [2ne] edge id per entry
+    DBuf edges;      // int32 [ne*2] (min, max)
+    DBuf face_edge;  // int32 [nf*3] edge opposite corner k
+    DBuf face_sign;  // int8 [nf*3]
+    DBuf edge_face;  // int32 [ne*2] faces of the edge, ascending; -1 absent
+    DBuf edge_slot;  // int32 [ne*2]
+    DBuf twin;       // int32 [nf*3] (other face << 2 | its slot) or -1 on boundary
+    DBuf Af;         // double [nf]
+    DBuf Av;         // double [nv]
+    DBuf theta;      // double [ne]
+    DBuf ev;         // float [ne*3] edge vector max - min (orientation halfedge)
+    DBuf gradop;     // float [nf*9] grad of corner k's hat function: (N x e_k)/(2A)
+    DBuf Aff;        // float [nf] face area
+};
+
+// Per-query workspace (BFS products, the level-ordered layout, solver state).
+struct QueryWs {
+    int64_t cap_nv = 0, cap_nf = 0, cap_ne = 0, cap_nnz = 0;
+    int fp64 = 0;
+    // breadth-first traversal
+    DBuf level, parent, order, pos, key, lvl_off, meta;  // meta: [0] nlev [1] nreach [2] err
+    // level-ordered Gauss-Seidel layout
+    DBuf grow;      // int32 [nv+1]
+    DBuf gent;      // {int32 col, T w} [2ne]
+    DBuf diag;      // T [nv]
+    DBuf tiles;     // int2 [nv + nv/TILE + 2] (level, start) sorted by (parity, level)
+    DBuf ptile;     // int32 [nv + 4] per-parity tile prefix over levels
+    DBuf U0, U1;    // XVal<T> [nv] ping-pong state
+    // stages
+    DBuf h;         // T [nf*3]
+    DBuf g0, g1;    // T [nf*3] face form
+    DBuf l0, l1;    // T [nf*9] face form dual per slot
+    DBuf z, w, lam; // T [nf*3] edge form
+    DBuf sz, x;     // T [ne] edge form
+    DBuf inc;       // double [nv]
+    DBuf d0, d1;    // double [nv]
+    DBuf n0, n1;    // int32 [nv]
+    DBuf resid;     // double [iters*2]
+    DBuf e1;        // double [1]
+    // host-side facts of the last run
+    int nlev = 0, nreach = 0, final_buf = 0, form = 1, admm_iters = 0, diagnostics = 0;
+    double t = 0.0;
+};
+
+struct MeshH {
+    Ctx *ctx = nullptr;
+    DevMesh m;
+    std::vector<QueryWs *> ws;   // one per query slot of the last batch
+    int last_k = 0;
+    double stage_ms[5] = {0, 0, 0, 0, 0};
+    double gs_kernel_ms = 0.0;   // the diffusion kernel alone, last solve
+};
+
+// ---------------------------------------------------------------- kernels (host launchers)
+
+constexpr int TILE = 256;  // vertices per Gauss-Seidel tile (one per thread)
+
+// scan.cu
+gh_status exclusive_scan_i32(Ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *total_host);
+gh_status exclusive_scan_u32_dev(Ctx *c, const int32_t *in, int32_t *out, int64_t n);
+
+// setup.cu
+gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_dev);
+
+// bfs.cu
+gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src);
+gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
+
+// gs.cu
+// ev0/ev1 (may be null) are recorded on the stream right around the kernel launch
+gh_status run_gs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, int sweeps, cudaEvent_t ev0, cudaEvent_t ev1);
+
+// stages.cu
+gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q);
+gh_status run_face_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu);
+gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu);
+gh_status run_integrate(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out_dev);
+gh_status run_heat_residual(Ctx *c, const DevMesh &m, QueryWs &q);
+
+// device status word shared by launchers (one int in device memory per context)
+int *dev_status(Ctx *c);
+gh_status check_status(Ctx *c, const char *stage);
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace gh

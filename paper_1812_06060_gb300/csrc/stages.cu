@@ -1,0 +1,536 @@
+// Stages after the diffusion: face-wise gradient normalisation (Alg. 1 line 2,
+// eq. HeatDiffusionNormalization), the face-based ADMM (Sec. 3.2), the
+// edge-based ADMM (Sec. 4.1), breadth-first integration (eq. IntegrationStep,
+// Sec. 4) and the heat residual E1 (eq. HeatSolutionError).
+#include "internal.cuh"
+
+namespace gh {
+
+namespace {
+
+constexpr int NT = 256;
+
+template <class T> __device__ __forceinline__ T ldexp_t(T x, int n);
+template <> __device__ __forceinline__ float ldexp_t<float>(float x, int n) { return ldexpf(x, n); }
+template <> __device__ __forceinline__ double ldexp_t<double>(double x, int n) { return ldexp(x, n); }
+template <class T> __device__ __forceinline__ T sqrt_t(T x);
+template <> __device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt(x); }
+
+// Geometry accessors: FP32 stages read the rounded per-face / per-edge
+// operators; FP64 stages recompute them from the FP64 positions.
+template <class T> struct Geo;
+template <> struct Geo<float> {
+    const float *gradop, *ev, *Af;
+    __device__ void grad(int64_t f, int k, float *g) const {
+        g[0] = gradop[9 * f + 3 * k]; g[1] = gradop[9 * f + 3 * k + 1]; g[2] = gradop[9 * f + 3 * k + 2];
+    }
+    __device__ void edge(int64_t e, float *v) const { v[0] = ev[3 * e]; v[1] = ev[3 * e + 1]; v[2] = ev[3 * e + 2]; }
+    __device__ float area(int64_t f) const { return Af[f]; }
+};
+template <> struct Geo<double> {
+    const double *P, *Af;
+    const int32_t *F, *edges;
+    __device__ void grad(int64_t f, int k, double *g) const {
+        const double *a = P + 3 * F[3 * f], *b = P + 3 * F[3 * f + 1], *c = P + 3 * F[3 * f + 2];
+        double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        double twoA = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        double N[3] = {n[0] / twoA, n[1] / twoA, n[2] / twoA};
+        const double *p1 = P + 3 * F[3 * f + (k + 1) % 3], *p2 = P + 3 * F[3 * f + (k + 2) % 3];
+        double e[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+        g[0] = (N[1] * e[2] - N[2] * e[1]) / twoA;
+        g[1] = (N[2] * e[0] - N[0] * e[2]) / twoA;
+        g[2] = (N[0] * e[1] - N[1] * e[0]) / twoA;
+    }
+    __device__ void edge(int64_t e, double *v) const {
+        const double *a = P + 3 * edges[2 * e], *b = P + 3 * edges[2 * e + 1];
+        v[0] = b[0] - a[0]; v[1] = b[1] - a[1]; v[2] = b[2] - a[2];
+    }
+    __device__ double area(int64_t f) const { return Af[f]; }
+};
+
+template <class T> Geo<T> make_geo(const DevMesh &m);
+template <> Geo<float> make_geo<float>(const DevMesh &m) {
+    return Geo<float>{ptr<float>(m.gradop), ptr<float>(m.ev), ptr<float>(m.Aff)};
+}
+template <> Geo<double> make_geo<double>(const DevMesh &m) {
+    return Geo<double>{ptr<double>(m.P), ptr<double>(m.Af), ptr<int32_t>(m.F), ptr<int32_t>(m.edges)};
+}
+
+// ------------------------------------------------------------------ normalise
+
+// h = -grad u / |grad u|, grad u = sum_k u_k grad B_k; the three values are
+// first brought to their largest exponent (exact); unreached faces get h = 0
+template <class T>
+__global__ void k_normalize(int64_t nf, const int32_t *__restrict__ F, const int32_t *__restrict__ pos,
+                            const XVal<T> *__restrict__ U, Geo<T> geo, T *h) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    XVal<T> u[3];
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) {
+        int q = pos[F[3 * f + k]];
+        if (q < 0) { ok = false; break; }
+        u[k] = U[q];
+    }
+    T g[3] = {0, 0, 0};
+    if (ok) {
+        int eref = kZeroExp;
+        for (int k = 0; k < 3; ++k)
+            if (u[k].m != T(0) && u[k].e > eref) eref = u[k].e;
+        for (int k = 0; k < 3; ++k) {
+            T b[3];
+            geo.grad(f, k, b);
+            T uk = ldexp_t<T>(u[k].m, u[k].e - eref);
+            g[0] += uk * b[0]; g[1] += uk * b[1]; g[2] += uk * b[2];
+        }
+    }
+    T len = sqrt_t<T>(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    for (int c = 0; c < 3; ++c) h[3 * f + c] = (len > T(0)) ? -g[c] / len : T(0);
+}
+
+// ------------------------------------------------------------------ face ADMM
+
+// One ADMM iteration per face (Y, G, lambda in the paper's order), reading
+// the previous iteration's g and lambda of the face and of its neighbours
+// across interior edges (buffers *_in) and writing the new ones (*_out).
+//   q = g - lambda/(mu alpha);  y = q + A'/(A + A') ebar (ebar . (q' - q))
+//   g = (2h + mu sum_k (y_k + lambda_k/(mu alpha))) / (2 + mu n)
+//   lambda_k += mu alpha (y_k - g)
+// Optional residual partials per block: [0] |alpha (y - g)|^2,
+// [1] |mu alpha (g - g_old)|^2 summed over interior slots.
+template <class T>
+__global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ face_edge,
+                                                  const int32_t *__restrict__ twin, Geo<T> geo, const T *__restrict__ h,
+                                                  const T *__restrict__ g_in, const T *__restrict__ l_in, T *g_out,
+                                                  T *l_out, T mu, double *part) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rp = 0.0, rd = 0.0;
+    if (f < nf) {
+        const T A = geo.area(f);
+        const T alpha = sqrt_t<T>(A);
+        T g[3] = {g_in[3 * f], g_in[3 * f + 1], g_in[3 * f + 2]};
+        T y[3][3], lam[3][3];
+        bool in[3];
+        T acc[3] = {0, 0, 0};
+        int n = 0;
+        for (int k = 0; k < 3; ++k) {
+            for (int c = 0; c < 3; ++c) lam[k][c] = l_in[9 * f + 3 * k + c];
+            int tw = twin[3 * f + k];
+            in[k] = tw >= 0;
+            if (!in[k]) continue;
+            int f2 = tw >> 2, k2 = tw & 3;
+            T A2 = geo.area(f2);
+            T a2 = sqrt_t<T>(A2);
+            T ev[3];
+            geo.edge(face_edge[3 * f + k], ev);
+            T il = T(1) / sqrt_t<T>(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
+            T eb[3] = {ev[0] * il, ev[1] * il, ev[2] * il};
+            T q[3], q2[3];
+            for (int c = 0; c < 3; ++c) {
+                q[c] = g[c] - lam[k][c] / (mu * alpha);
+                q2[c] = g_in[3 * f2 + c] - l_in[9 * f2 + 3 * k2 + c] / (mu * a2);
+            }
+            T proj = eb[0] * (q2[0] - q[0]) + eb[1] * (q2[1] - q[1]) + eb[2] * (q2[2] - q[2]);
+            T wgt = A2 / (A + A2);
+            for (int c = 0; c < 3; ++c) {
+                y[k][c] = q[c] + wgt * eb[c] * proj;
+                acc[c] += y[k][c] + lam[k][c] / (mu * alpha);
+            }
+            ++n;
+        }
+        T gn[3];
+        for (int c = 0; c < 3; ++c) gn[c] = (T(2) * h[3 * f + c] + mu * acc[c]) / (T(2) + mu * T(n));
+        for (int c = 0; c < 3; ++c) g_out[3 * f + c] = gn[c];
+        for (int k = 0; k < 3; ++k) {
+            for (int c = 0; c < 3; ++c) {
+                T lk = lam[k][c];
+                if (in[k]) {
+                    T r = alpha * (y[k][c] - gn[c]);
+                    lk += mu * r;
+                    rp += (double)r * (double)r;
+                    double dgv = (double)mu * (double)alpha * ((double)gn[c] - (double)g[c]);
+                    rd += dgv * dgv;
+                }
+                l_out[9 * f + 3 * k + c] = lk;
+            }
+        }
+    }
+    if (part) {
+        __shared__ double s0[NT], s1[NT];
+        s0[threadIdx.x] = rp;
+        s1[threadIdx.x] = rd;
+        __syncthreads();
+        for (int o = NT / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
+    }
+}
+
+template <class T>
+__global__ void k_face_init(int64_t nf, const T *__restrict__ h, T *g, T *l) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    for (int c = 0; c < 3; ++c) g[3 * f + c] = h[3 * f + c];
+    for (int c = 0; c < 9; ++c) l[9 * f + c] = T(0);
+}
+
+// ------------------------------------------------------------------ edge ADMM
+
+// z = h . e per face slot, e the orientation-halfedge vector (max - min)
+// (eq. TargetDifference); w = z, lambda = 0
+template <class T>
+__global__ void k_edge_targets(int64_t nf, const int32_t *__restrict__ face_edge, Geo<T> geo, const T *__restrict__ h,
+                               T *z, T *w, T *lam) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    for (int k = 0; k < 3; ++k) {
+        T ev[3];
+        geo.edge(face_edge[3 * f + k], ev);
+        T zz = h[3 * f] * ev[0] + h[3 * f + 1] * ev[1] + h[3 * f + 2] * ev[2];
+        z[3 * f + k] = zz;
+        w[3 * f + k] = zz;
+        lam[3 * f + k] = T(0);
+    }
+}
+
+// sum of targets per edge and x = their mean
+template <class T>
+__global__ void k_edge_init(int64_t ne, const int32_t *__restrict__ edge_face, const int32_t *__restrict__ edge_slot,
+                            const T *__restrict__ z, T *sz, T *x) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    T s = 0;
+    int n = 0;
+    for (int j = 0; j < 2; ++j) {
+        int f = edge_face[2 * e + j];
+        if (f >= 0) { s += z[3 * f + edge_slot[2 * e + j]]; ++n; }
+    }
+    sz[e] = s;
+    x[e] = s / T(n);
+}
+
+// face pass of iteration it: the lambda-update of iteration it-1
+// (lambda += mu (w - x)) then the W-update w = (I - q q^T/3)(x_f - lambda/mu)
+template <class T>
+__global__ void k_edge_face_pass(int64_t nf, const int32_t *__restrict__ face_edge, const int8_t *__restrict__ sign,
+                                 const T *__restrict__ x, T *w, T *lam, T mu, int do_lambda) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    T v[3], q[3];
+    T qv = 0;
+    for (int k = 0; k < 3; ++k) {
+        T xk = x[face_edge[3 * f + k]];
+        T l = lam[3 * f + k];
+        if (do_lambda) {
+            l += mu * (w[3 * f + k] - xk);
+            lam[3 * f + k] = l;
+        }
+        v[k] = xk - l / mu;
+        q[k] = (T)sign[3 * f + k];
+        qv += q[k] * v[k];
+    }
+    for (int k = 0; k < 3; ++k) w[3 * f + k] = v[k] - q[k] * qv / T(3);
+}
+
+// X-update (eq. xeupdate): x_e = (sum z + sum (lambda + mu w)) / (n_e (1 + mu));
+// optional residual partials per block: [0] sum (w - x)^2, [1] sum (mu dx)^2
+// over the edge's slots
+template <class T>
+__global__ void __launch_bounds__(NT) k_edge_edge_pass(int64_t ne, const int32_t *__restrict__ edge_face,
+                                                       const int32_t *__restrict__ edge_slot, const T *__restrict__ sz,
+                                                       const T *__restrict__ w, const T *__restrict__ lam, T *x, T mu,
+                                                       double *part) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rp = 0.0, rd = 0.0;
+    if (e < ne) {
+        T s = sz[e];
+        int n = 0;
+        int sl[2];
+        for (int j = 0; j < 2; ++j) {
+            int f = edge_face[2 * e + j];
+            sl[j] = -1;
+            if (f >= 0) {
+                sl[j] = 3 * f + edge_slot[2 * e + j];
+                s += lam[sl[j]] + mu * w[sl[j]];
+                ++n;
+            }
+        }
+        T xo = x[e];
+        T xn = s / (T(n) * (T(1) + mu));
+        x[e] = xn;
+        if (part) {
+            for (int j = 0; j < 2; ++j) {
+                if (sl[j] < 0) continue;
+                double r = (double)w[sl[j]] - (double)xn;
+                rp += r * r;
+                double d = (double)mu * ((double)xn - (double)xo);
+                rd += d * d;
+            }
+        }
+    }
+    if (part) {
+        __shared__ double s0[NT], s1[NT];
+        s0[threadIdx.x] = rp;
+        s1[threadIdx.x] = rd;
+        __syncthreads();
+        for (int o = NT / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
+    }
+}
+
+// sum per-block residual partials in a fixed order: out = sqrt(sum)
+__global__ void k_resid_final(const double *__restrict__ part, int nblocks, double *out) {
+    __shared__ double s0[NT], s1[NT];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += NT) { a += part[2 * i]; b += part[2 * i + 1]; }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = sqrt(s0[0]); out[1] = sqrt(s1[0]); }
+}
+
+// ------------------------------------------------------------------ integration
+
+__device__ __forceinline__ int find_in_row(const int32_t *__restrict__ col, int b, int e, int x) {
+    while (b < e) {
+        int m = (b + e) >> 1;
+        int c = col[m];
+        if (c == x) return m;
+        if (c < x) b = m + 1; else e = m;
+    }
+    return -1;
+}
+
+// increment of each vertex over its breadth-first pairing vertex k:
+// face form  1/|T| sum_{f in T_jk} g_f . (p_j - p_k)   (eq. IntegrationStep)
+// edge form  +x_e if v_j is the head of the orientation halfedge, else -x_e
+template <class T>
+__global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, const int32_t *__restrict__ parent,
+                             const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                             const int32_t *__restrict__ col_edge, const int32_t *__restrict__ edges,
+                             const int32_t *__restrict__ edge_face, const double *__restrict__ P,
+                             const T *__restrict__ g, const T *__restrict__ x, int form, double *inc, int32_t *nxt,
+                             double *d) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    int lv = level[v];
+    if (lv <= 0) {
+        inc[v] = 0.0;
+        nxt[v] = -1;
+        d[v] = (lv == 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
+        return;
+    }
+    int p = parent[v];
+    int j = find_in_row(col, rowptr[v], rowptr[v + 1], p);
+    if (j < 0) {  // cannot happen for a breadth-first pairing; keeps the access in bounds
+        inc[v] = 0.0;
+        nxt[v] = -1;
+        d[v] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    int e = col_edge[j];
+    double dv;
+    if (form == GH_FORM_EDGE) {
+        double xe = (double)x[e];
+        dv = (edges[2 * e + 1] == (int)v) ? xe : -xe;
+    } else {
+        double dp[3] = {P[3 * v] - P[3 * p], P[3 * v + 1] - P[3 * p + 1], P[3 * v + 2] - P[3 * p + 2]};
+        double s = 0.0;
+        int n = 0;
+        for (int a = 0; a < 2; ++a) {
+            int f = edge_face[2 * e + a];
+            if (f < 0) continue;
+            s += (double)g[3 * f] * dp[0] + (double)g[3 * f + 1] * dp[1] + (double)g[3 * f + 2] * dp[2];
+            ++n;
+        }
+        dv = s / n;
+    }
+    inc[v] = dv;
+    nxt[v] = p;
+    d[v] = dv;
+}
+
+// Sum of the increments along each vertex's chain of pairing vertices by
+// pointer jumping: after round r, d[v] holds the sum over the first 2^r
+// links and nxt[v] the vertex 2^r links up.  All sets are integrated in
+// ceil(log2 L) rounds instead of L dependent steps.
+__global__ void k_jump(int64_t nv, const double *__restrict__ d_in, const int32_t *__restrict__ n_in, double *d_out,
+                       int32_t *n_out) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    int nx = n_in[v];
+    if (nx >= 0) {
+        d_out[v] = d_in[v] + d_in[nx];
+        n_out[v] = n_in[nx];
+    } else {
+        d_out[v] = d_in[v];
+        n_out[v] = -1;
+    }
+}
+
+// ------------------------------------------------------------------ heat residual
+
+// per reached vertex r (queue order): (A - t L_c) u - u_0 in FP64
+template <class T>
+__global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restrict__ grow, const int32_t *__restrict__ gcol,
+                                                   const T *__restrict__ gw, const T *__restrict__ diag,
+                                                   const int32_t *__restrict__ lvl_off, const XVal<T> *__restrict__ U,
+                                                   double *part) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (r < n) {
+        XVal<T> ur = U[r];
+        double uv = ldexp((double)ur.m, max(ur.e, -2000));
+        double res = (double)diag[r] * uv;
+        for (int a = grow[r]; a < grow[r + 1]; ++a) {
+            XVal<T> uc = U[gcol[a]];
+            res -= (double)gw[a] * ldexp((double)uc.m, max(uc.e, -2000));
+        }
+        if (r < lvl_off[1]) res -= 1.0;
+        acc = res * res;
+    }
+    __shared__ double s[NT];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s[0]; part[2 * blockIdx.x + 1] = 0.0; }
+}
+
+template <class T> gh_status normalize_t(Ctx *c, const DevMesh &m, QueryWs &q) {
+    const XVal<T> *U = ptr<XVal<T>>(q.final_buf ? q.U1 : q.U0);
+    k_normalize<T><<<blocks_for(m.nf, NT), NT, 0, c->stream>>>(m.nf, ptr<int32_t>(m.F), ptr<int32_t>(q.pos), U,
+                                                              make_geo<T>(m), ptr<T>(q.h)); ++c->launches;
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+template <class T> gh_status face_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+    cudaStream_t st = c->stream;
+    unsigned nb = blocks_for(m.nf, NT);
+    T *g[2] = {ptr<T>(q.g0), ptr<T>(q.g1)};
+    T *l[2] = {ptr<T>(q.l0), ptr<T>(q.l1)};
+    k_face_init<T><<<nb, NT, 0, st>>>(m.nf, ptr<T>(q.h), g[0], l[0]); ++c->launches;
+    double *part = nullptr;
+    if (q.diagnostics) GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
+    Geo<T> geo = make_geo<T>(m);
+    for (int it = 0; it < iters; ++it) {
+        int a = it & 1;
+        k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), ptr<int32_t>(m.twin), geo, ptr<T>(q.h),
+                                          g[a], l[a], g[a ^ 1], l[a ^ 1], (T)mu, part); ++c->launches;
+        if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it); ++c->launches; }
+    }
+    if (part) cudaFreeAsync(part, st);
+    q.admm_iters = iters;
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+    cudaStream_t st = c->stream;
+    unsigned nbf = blocks_for(m.nf, NT), nbe = blocks_for(m.ne, NT);
+    Geo<T> geo = make_geo<T>(m);
+    k_edge_targets<T><<<nbf, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), geo, ptr<T>(q.h), ptr<T>(q.z), ptr<T>(q.w),
+                                          ptr<T>(q.lam)); ++c->launches;
+    k_edge_init<T><<<nbe, NT, 0, st>>>(m.ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot), ptr<T>(q.z),
+                                       ptr<T>(q.sz), ptr<T>(q.x)); ++c->launches;
+    double *part = nullptr;
+    if (q.diagnostics) GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nbe, st));
+    for (int it = 0; it < iters; ++it) {
+        k_edge_face_pass<T><<<nbf, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), ptr<int8_t>(m.face_sign),
+                                                ptr<T>(q.x), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, it > 0); ++c->launches;
+        k_edge_edge_pass<T><<<nbe, NT, 0, st>>>(m.ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
+                                                ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x), (T)mu, part); ++c->launches;
+        if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nbe, ptr<double>(q.resid) + 2 * it); ++c->launches; }
+    }
+    if (part) cudaFreeAsync(part, st);
+    q.admm_iters = iters;
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out) {
+    cudaStream_t st = c->stream;
+    unsigned nb = blocks_for(m.nv, NT);
+    double *d[2] = {ptr<double>(q.d0), ptr<double>(q.d1)};
+    int32_t *n[2] = {ptr<int32_t>(q.n0), ptr<int32_t>(q.n1)};
+    k_increments<T><<<nb, NT, 0, st>>>(m.nv, ptr<int32_t>(q.level), ptr<int32_t>(q.parent), ptr<int32_t>(m.rowptr),
+                                       ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge), ptr<int32_t>(m.edges),
+                                       ptr<int32_t>(m.edge_face), ptr<double>(m.P), ptr<T>(q.g0), ptr<T>(q.x), q.form,
+                                       ptr<double>(q.inc), n[0], d[0]); ++c->launches;
+    int rounds = 0;
+    while ((1 << rounds) < q.nlev) ++rounds;
+    int cur = 0;
+    for (int r = 0; r < rounds; ++r) {
+        k_jump<<<nb, NT, 0, st>>>(m.nv, d[cur], n[cur], d[cur ^ 1], n[cur ^ 1]); ++c->launches;
+        cur ^= 1;
+    }
+    // the workspace keeps the result in d0 (read by gh_debug_dump)
+    if (cur == 1) GH_CUDA(cudaMemcpyAsync(d[0], d[1], sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
+    if (d_out) GH_CUDA(cudaMemcpyAsync(d_out, d[0], sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+template <class T> gh_status heat_resid_t(Ctx *c, QueryWs &q) {
+    cudaStream_t st = c->stream;
+    int n = q.nreach;
+    unsigned nb = blocks_for(n, NT);
+    double *part = nullptr;
+    GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
+    const int32_t *gcol = ptr<int32_t>(q.gent);
+    const T *gw = reinterpret_cast<const T *>(gcol + q.cap_nnz);
+    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.grow), gcol, gw, ptr<T>(q.diag), ptr<int32_t>(q.lvl_off),
+                                       ptr<XVal<T>>(q.final_buf ? q.U1 : q.U0), part); ++c->launches;
+    double *tmp = nullptr;
+    GH_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * 2, st));
+    k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, tmp); ++c->launches;
+    GH_CUDA(cudaMemcpyAsync(q.e1.p, tmp, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    cudaFreeAsync(part, st);
+    cudaFreeAsync(tmp, st);
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+}  // namespace
+
+gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q) {
+    return q.fp64 ? normalize_t<double>(c, m, q) : normalize_t<float>(c, m, q);
+}
+gh_status run_face_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+    q.form = GH_FORM_FACE;
+    gh_status s = q.fp64 ? face_admm_t<double>(c, m, q, iters, mu) : face_admm_t<float>(c, m, q, iters, mu);
+    if (s != GH_OK) return s;
+    // the result of the last iteration is in buffer (iters & 1); keep it in g0
+    if (iters & 1) {
+        size_t es = q.fp64 ? sizeof(double) : sizeof(float);
+        GH_CUDA(cudaMemcpyAsync(q.g0.p, q.g1.p, es * 3 * m.nf, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return GH_OK;
+}
+gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+    q.form = GH_FORM_EDGE;
+    return q.fp64 ? edge_admm_t<double>(c, m, q, iters, mu) : edge_admm_t<float>(c, m, q, iters, mu);
+}
+gh_status run_integrate(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out_dev) {
+    return q.fp64 ? integrate_t<double>(c, m, q, d_out_dev) : integrate_t<float>(c, m, q, d_out_dev);
+}
+gh_status run_heat_residual(Ctx *c, const DevMesh &m, QueryWs &q) {
+    (void)m;
+    return q.fp64 ? heat_resid_t<double>(c, q) : heat_resid_t<float>(c, q);
+}
+
+}  // namespace gh

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Contract: connectivity, breadth-first sets, pairing and queue order are
+bit-exact; distances agree within 1e-4 relative to max(|d*|, hbar) away from
+the sources in FP32 mode and within 1e-9 in FP64 mode, at equal iteration
+counts.  Intermediates (u, h, g, x) are checked with bounds derived from the
+arithmetic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+D_TOL_FP32 = 1e-4
+D_TOL_FP64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def gh():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_06060_gb300 import build
+    build.build()
+    import paper_1812_06060_gb300 as g
+    g.load_library()
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(gh):
+    c = gh.Context(0)
+    yield c
+    c.close()
+
+
+def _u_rel_err(um_g, ue_g, um_o, ue_o):
+    """|u_gpu / u_oracle - 1| elementwise with both in (mantissa, exponent)."""
+    nz = um_o != 0
+    out = np.zeros(um_o.shape)
+    d = np.clip(ue_g[nz].astype(np.int64) - ue_o[nz].astype(np.int64), -1000, 1000)
+    out[nz] = np.abs(np.ldexp(um_g[nz], d) / um_o[nz] - 1.0)
+    return out
+
+
+def _d_err(d, dref, sources, hbar):
+    mask = np.isfinite(dref)
+    mask[np.asarray(sources)] = False
+    den = np.maximum(np.abs(dref[mask]), hbar)
+    return np.max(np.abs(d[mask] - dref[mask]) / den) if mask.any() else 0.0
+
+
+def _check_setup(mesh_g, md):
+    g = mesh_g
+    assert g.nv == md.nv and g.ne == md.ne and g.nf == md.nf
+    assert math.isclose(g.hbar, md.hbar, rel_tol=1e-13)
+    assert np.array_equal(g.dump(g_mod.GH_DUMP_EDGES).reshape(-1, 2), md.edges)
+    assert np.array_equal(g.dump(g_mod.GH_DUMP_FACE_EDGE).reshape(-1, 3), md.face_edge)
+    assert np.array_equal(g.dump(g_mod.GH_DUMP_FACE_SIGN).reshape(-1, 3), md.face_sign.astype(np.int32))
+    assert np.array_equal(g.dump(g_mod.GH_DUMP_ROWPTR), md.rowptr)
+    assert np.array_equal(g.dump(g_mod.GH_DUMP_COL), md.col)
+    assert np.allclose(g.dump(g_mod.GH_DUMP_THETA), md.theta, rtol=1e-12, atol=1e-14)
+    assert np.allclose(g.dump(g_mod.GH_DUMP_AV), md.Av, rtol=1e-12, atol=0)
+    assert np.allclose(g.dump(g_mod.GH_DUMP_AF), md.Af, rtol=1e-12, atol=0)
+
+
+g_mod = None
+
+
+def _run_case(gh, ctx, mesh, sources, form, sweeps, fp64, tol, admm_iters=10):
+    global g_mod
+    g_mod = gh
+    md = oracle.mesh_data(mesh.V, mesh.F)
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    try:
+        d = np.empty(md.nv)
+        M.solve(np.asarray(sources, np.int32), d, gh.params(gs_sweeps=sweeps, form=form, fp64=fp64,
+                                                           admm_iters=admm_iters))
+        ref = oracle.solve(md, sources, form, sweeps=sweeps, admm_iters=admm_iters)
+        b = ref["bfs"]
+        _check_setup(M, md)
+        # breadth-first products: bit-exact
+        assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL), b.level)
+        assert np.array_equal(M.dump(gh.GH_DUMP_PARENT), b.parent)
+        assert np.array_equal(M.dump(gh.GH_DUMP_ORDER), b.order)
+        assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL_OFF), b.level_off)
+        assert M.dump(gh.GH_DUMP_T)[0] == pytest.approx(ref["t"], rel=1e-15)
+        # diffusion state
+        um, ue = M.dump(gh.GH_DUMP_U_MANT), M.dump(gh.GH_DUMP_U_EXP)
+        uerr = _u_rel_err(um, ue, ref["u"][0], ref["u"][1])
+        # distances: the contract
+        derr = _d_err(d, ref["d"], sources, md.hbar)
+        assert np.array_equal(np.isinf(d), np.isinf(ref["d"]))
+        assert np.all(d[np.asarray(sources)] == 0)
+        return dict(uerr=uerr.max(), derr=derr, h=M.dump(gh.GH_DUMP_H).reshape(-1, 3), href=ref["h"],
+                    M=M, md=md, ref=ref, d=d)
+    finally:
+        pass
+
+
+def _h_err(h, href):
+    return np.max(np.linalg.norm(h - href, axis=1))
+
+
+@pytest.mark.parametrize("form", ["face", "edge"])
+def test_icosphere4_fp64(gh, ctx, form):
+    """Unit icosphere level 4, source vertex 0, t = hbar^2, FP64 mode."""
+    w = meshgen.workload_c1()
+    r = _run_case(gh, ctx, w.mesh, [0], form, 200, True, D_TOL_FP64)
+    assert r["uerr"] < 1e-12
+    assert _h_err(r["h"], r["href"]) < 1e-10
+    assert r["derr"] < D_TOL_FP64
+    r["M"].close()
+
+
+@pytest.mark.parametrize("form", ["face", "edge"])
+def test_icosphere4_fp32(gh, ctx, form):
+    w = meshgen.workload_c1()
+    r = _run_case(gh, ctx, w.mesh, [0], form, 200, False, D_TOL_FP32)
+    assert r["uerr"] < 1e-4
+    assert r["derr"] < D_TOL_FP32
+    r["M"].close()
+
+
+@pytest.mark.parametrize("form", ["face", "edge"])
+def test_jittered_grid_ragged(gh, ctx, form):
+    """129^2 jittered grid: many tiles per set and ragged set ends; enough
+    sweeps for the values to span far below the FP32 exponent range."""
+    m = meshgen.jittered_grid(129, 77)
+    r = _run_case(gh, ctx, m, [4000], form, 600, False, D_TOL_FP32)
+    assert r["ref"]["u"][1].min() < -300          # needs the separate exponent in FP32
+    assert r["uerr"] < 1e-3
+    assert r["derr"] < D_TOL_FP32
+    r["M"].close()
+
+
+@pytest.mark.parametrize("form", ["face", "edge"])
+def test_noisy_sphere_multi_source(gh, ctx, form):
+    m = meshgen.noisy_icosphere(5, 31)
+    r = _run_case(gh, ctx, m, [17, 5000, 9999], form, 300, False, D_TOL_FP32)
+    assert r["derr"] < D_TOL_FP32
+    r["M"].close()
+
+
+def test_small_odd_grid_and_two_components(gh, ctx):
+    g = meshgen.jittered_grid(37, 3)
+    V = np.concatenate([g.V, g.V + [2.0, 0.0, 0.0]])
+    F = np.concatenate([g.F, g.F + g.nv]).astype(np.int32)
+    mesh = meshgen.Mesh(V, F)
+    r = _run_case(gh, ctx, mesh, [5, 700], "edge", 150, False, D_TOL_FP32)
+    assert np.all(np.isinf(r["d"][g.nv:]))
+    assert r["derr"] < D_TOL_FP32
+    r["M"].close()
+
+
+def test_batch_equals_single_solves(gh, ctx):
+    m = meshgen.noisy_icosphere(4, 8)
+    rng = meshgen.rng_for(5)
+    sets = [meshgen.random_sources(rng, m.nv, 1, 8) for _ in range(6)]
+    M = gh.Mesh(ctx, m.V, m.F)
+    prm = gh.params(gs_sweeps=120, form="edge")
+    out = np.empty((len(sets), m.nv))
+    M.solve_batch(sets, out, prm)
+    md = oracle.mesh_data(m.V, m.F)
+    for q, s in enumerate(sets):
+        one = np.empty(m.nv)
+        M.solve(s, one, prm)
+        assert np.array_equal(one, out[q])
+        ref = oracle.solve(md, s, "edge", sweeps=120)
+        assert _d_err(out[q], ref["d"], s, md.hbar) < D_TOL_FP32
+    M.close()
+
+
+def test_deterministic_and_device_buffers(gh, ctx):
+    import torch
+    m = meshgen.noisy_icosphere(4, 2)
+    M = gh.Mesh(ctx, torch.from_numpy(m.V).cuda(), torch.from_numpy(m.F).cuda())
+    src = torch.tensor([3, 77], dtype=torch.int32, device="cuda")
+    prm = gh.params(gs_sweeps=90, form="face")
+    a = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+    b = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+    M.solve(src, a, prm)
+    M.solve(src, b, prm)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    h = np.empty(m.nv)
+    M.solve(np.array([3, 77], np.int32), h, prm)
+    assert np.array_equal(h, a.cpu().numpy())
+    M.close()
+
+
+def test_diagnostics(gh, ctx):
+    w = meshgen.workload_c1()
+    md = oracle.mesh_data(w.mesh.V, w.mesh.F)
+    M = gh.Mesh(ctx, w.mesh.V, w.mesh.F)
+    for form in ("face", "edge"):
+        d = np.empty(md.nv)
+        M.solve([0], d, gh.params(gs_sweeps=200, form=form, fp64=True, diagnostics=True))
+        ref = oracle.solve(md, [0], form, sweeps=200)
+        res = M.dump(gh.GH_DUMP_RESID).reshape(-1, 2)
+        assert np.allclose(res, ref["res"][:, :2], rtol=1e-8, atol=1e-14)
+        e1 = M.dump(gh.GH_DUMP_E1)[0]
+        assert e1 == pytest.approx(oracle.heat_residual(md, ref["bfs"], ref["t"], ref["u"]), rel=1e-6, abs=1e-15)
+    M.close()
+
+
+def test_errors(gh, ctx):
+    m = meshgen.icosphere(2)
+    M = gh.Mesh(ctx, m.V, m.F)
+    d = np.empty(m.nv)
+    with pytest.raises(gh.GeoheatError) as e:
+        M.solve(np.array([m.nv], np.int32), d, gh.params())
+    assert e.value.status == gh.GH_EINVAL
+    with pytest.raises(gh.GeoheatError) as e:
+        M.solve(np.array([0], np.int32), d, gh.params(gs_sweeps=0))
+    assert e.value.status == gh.GH_EINVAL
+    M.close()
+    V = np.zeros((5, 3))
+    V[:, 0] = [0, 1, 0, 0, 1]
+    V[:, 1] = [0, 0, 1, -1, 1]
+    with pytest.raises(gh.GeoheatError) as e:
+        gh.Mesh(ctx, V, np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], np.int32))
+    assert e.value.status == gh.GH_ENONMANIFOLD
+    with pytest.raises(gh.GeoheatError) as e:
+        gh.Mesh(ctx, V, np.array([[0, 1, 2], [0, 1, 3]], np.int32))
+    assert e.value.status == gh.GH_ENONMANIFOLD
+    with pytest.raises(gh.GeoheatError) as e:
+        gh.Mesh(ctx, V, np.array([[0, 1, 9]], np.int32))
+    assert e.value.status == gh.GH_EINVAL
+
+
+def test_full_size_grid_1025(gh, ctx):
+    """The 1025^2 jittered grid of the benchmark at full size, in the launch
+    configuration the benchmark times, with a reduced sweep count so the
+    oracle runs in seconds: bit-exact sets, distances within the contract."""
+    w = meshgen.workload_c2()
+    r = _run_case(gh, ctx, w.mesh, list(w.sources[0]), "edge", 40, False, D_TOL_FP32)
+    assert r["derr"] < D_TOL_FP32
+    r["M"].close()
