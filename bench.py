@@ -317,13 +317,19 @@ def run_ours(args):
 
 
 def main():
+    global SWEEPS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=SWEEPS,
+                    help="Gauss-Seidel sweeps per solve (a smaller case for profiling; the benchmark is 2000)")
     args = ap.parse_args()
+    if args.sweeps != SWEEPS:
+        WORKLOAD = WORKLOAD.replace(f"{SWEEPS} Gauss-Seidel", f"{args.sweeps} Gauss-Seidel")
+        SWEEPS = args.sweeps
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

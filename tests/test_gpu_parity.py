@@ -133,7 +133,7 @@ def test_jittered_grid_ragged(gh, ctx, form):
     sweeps for the values to span far below the FP32 exponent range."""
     m = meshgen.jittered_grid(129, 77)
     r = _run_case(gh, ctx, m, [4000], form, 600, False, D_TOL_FP32)
-    assert r["ref"]["u"][1].min() < -300          # needs the separate exponent in FP32
+    assert r["ref"]["u"][1].min() < -150          # below the FP32 range: needs the separate exponent
     assert r["uerr"] < 1e-3
     assert r["derr"] < D_TOL_FP32
     r["M"].close()
