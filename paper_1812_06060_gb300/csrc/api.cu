@@ -113,8 +113,9 @@ static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int f
 #define A(buf, bytes) if ((s = dalloc(c, w.buf, (size_t)(bytes))) != GH_OK) return s
     A(level, 4 * nv); A(parent, 4 * nv); A(order, 4 * nv); A(pos, 4 * nv); A(key, 8 * nv);
     A(lvl_off, 4 * (nv + 2)); A(meta, 16);
-    A(grow, 4 * (nv + 1)); A(gent, nnz * (4 + es)); A(diag, es * nv);
-    A(tiles, 8 * (nv + nv / TILE + 4)); A(ptile, 4 * (nv + 8));
+    // padded so 16-byte aligned bulk copies of any row window stay inside the buffers
+    A(grow, 4 * (nv + 9)); A(gent, (nnz + 4) * (fp64 ? 16 : 8)); A(diag, es * (nv + 4));
+    A(ptile, 4 * (nv + 8));
     A(U0, xs * nv); A(U1, xs * nv);
     A(h, es * 3 * nf);
     if (form == GH_FORM_FACE) {
@@ -142,7 +143,7 @@ static gh_status validate_params(const gh_params *p) {
 static size_t ws_bytes(const DevMesh &m, int fp64, int form) {
     const size_t es = fp64 ? 8 : 4, xs = fp64 ? 16 : 8;
     size_t nv = m.nv, nf = m.nf, ne = m.ne;
-    size_t b = nv * (4 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (4 + es) + es * 3 * nf;
+    size_t b = nv * (4 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) + es * 3 * nf;
     b += (form == GH_FORM_FACE) ? es * 24 * nf : es * (9 * nf + 2 * ne);
     return b + (1 << 20);
 }

@@ -142,7 +142,7 @@ __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const in
                               const int32_t *__restrict__ col, const int32_t *__restrict__ col_edge,
                               const double *__restrict__ theta, const double *__restrict__ Av,
                               const int32_t *__restrict__ pos, const int32_t *__restrict__ grow, double t,
-                              int32_t *gcol, T *gw, T *diag) {
+                              Ent<T> *gent, T *diag) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int v = order[r];
@@ -151,8 +151,10 @@ __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const in
     for (int j = b; j < e; ++j) {
         double th = theta[col_edge[j]];
         sum += th;
-        gcol[o + (j - b)] = pos[col[j]];
-        gw[o + (j - b)] = (T)(t * th);
+        Ent<T> x;
+        x.col = pos[col[j]];
+        x.w = (T)(t * th);
+        gent[o + (j - b)] = x;
     }
     diag[r] = (T)(Av[v] + t * sum);
 }
@@ -160,8 +162,12 @@ __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const in
 // tiles of at most TILE queue positions inside one set, listed set by set,
 // even sets first, then odd sets; ptile holds, per parity, the running tile
 // count before each set of that parity
-__global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_off, int nlev, int32_t *ptile,
-                                              int2 *tiles) {
+__device__ __forceinline__ int ntiles_of(const int32_t *lvl_off, int nlev, int i) {
+    return (i < 0 || i >= nlev) ? 0 : (lvl_off[i + 1] - lvl_off[i] + TILE - 1) / TILE;
+}
+
+__global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_off, int nlev,
+                                              const int32_t *__restrict__ grow, int32_t *ptile, TileDesc *tiles) {
     int n_even = (nlev + 1) / 2, n_odd = nlev / 2;
     int32_t *p0 = ptile, *p1 = ptile + n_even + 1;
     for (int par = 0; par < 2; ++par) {
@@ -170,12 +176,7 @@ __global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_of
         int carry = 0;
         for (int c0 = 0; c0 < nl; c0 += BT) {
             int j = c0 + threadIdx.x;
-            int cnt = 0;
-            if (j < nl) {
-                int i = par + 2 * j;
-                int sz = lvl_off[i + 1] - lvl_off[i];
-                cnt = (sz + TILE - 1) / TILE;
-            }
+            int cnt = (j < nl) ? ntiles_of(lvl_off, nlev, par + 2 * j) : 0;
             int excl;
             int tot = bt_scan(cnt, excl);
             if (j < nl) pp[j] = carry + excl;
@@ -189,7 +190,21 @@ __global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_of
         int par = i & 1, j = i >> 1;
         int first = (par ? base1 + p1[j] : p0[j]);
         int s = lvl_off[i], e = lvl_off[i + 1];
-        for (int k = 0; s + k * TILE < e; ++k) tiles[first + k] = make_int2(i, s + k * TILE);
+        int ntp = ntiles_of(lvl_off, nlev, i - 1), nts = ntiles_of(lvl_off, nlev, i), ntn = ntiles_of(lvl_off, nlev, i + 1);
+        for (int k = 0; s + k * TILE < e; ++k) {
+            TileDesc d;
+            d.level = i;
+            d.start = s + k * TILE;
+            d.count = min(TILE, e - d.start);
+            d.lo = s;
+            d.eb = grow[d.start];
+            d.ee = grow[d.start + d.count];
+            d.nt_prev = ntp;
+            d.nt_self = nts;
+            d.nt_next = ntn;
+            d.pad0 = d.pad1 = d.pad2 = 0;
+            tiles[first + k] = d;
+        }
     }
 }
 
@@ -238,21 +253,21 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
     k_row_len<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), len); ++c->launches;
     gh_status s = exclusive_scan_u32_dev(c, len, ptr<int32_t>(q.grow), n);
     if (s != GH_OK) return s;
-    int32_t *gcol = ptr<int32_t>(q.gent);
     if (q.fp64) {
-        double *gw = reinterpret_cast<double *>(gcol + q.cap_nnz);
         k_fill_layout<double><<<blocks_for(n, 256), 256, 0, st>>>(
             ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
-            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t, gcol, gw,
-            ptr<double>(q.diag)); ++c->launches;
+            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t,
+            ptr<Ent<double>>(q.gent), ptr<double>(q.diag)); ++c->launches;
     } else {
-        float *gw = reinterpret_cast<float *>(gcol + q.cap_nnz);
         k_fill_layout<float><<<blocks_for(n, 256), 256, 0, st>>>(
             ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
-            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t, gcol, gw,
-            ptr<float>(q.diag)); ++c->launches;
+            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t,
+            ptr<Ent<float>>(q.gent), ptr<float>(q.diag)); ++c->launches;
     }
-    k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.ptile), ptr<int2>(q.tiles)); ++c->launches;
+    s = dalloc(c, q.tiles, sizeof(TileDesc) * ((size_t)n / TILE + (size_t)q.nlev + 2));
+    if (s != GH_OK) return s;
+    k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.grow), ptr<int32_t>(q.ptile),
+                              ptr<TileDesc>(q.tiles)); ++c->launches;
     GH_CUDA(cudaGetLastError());
     q.t = t;
     return GH_OK;

@@ -34,6 +34,8 @@
 // is exact, so this is the same arithmetic with an unbounded exponent.
 #include <cooperative_groups.h>
 
+#include <cstddef>
+
 #include "internal.cuh"
 
 namespace gh {
@@ -51,12 +53,11 @@ template <class T> struct GsJob {
     int cta0, ncta;        // the CTAs serving this query
     const int32_t *lvl_off;
     const int32_t *grow;
-    const int32_t *gcol;
-    const T *gw;
+    const Ent<T> *gent;
     const T *diag;
     const int32_t *ptile0;
     const int32_t *ptile1;
-    const int2 *tiles;
+    const TileDesc *tiles;
     const int32_t *stepoff;  // [nsteps + 1] first tile number of each step
     int32_t *done;           // [nlev] finished tiles per set
     XVal<T> *U[2];
@@ -76,25 +77,6 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
 
 __device__ __forceinline__ void red_release_add(int32_t *p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Wait until *p >= target; bounded: on timeout (or when another CTA gave up)
-// raise the abort flag and the status word and return false.
-__device__ bool wait_ge(const int32_t *p, int target, int *abort_flag, int *status) {
-    if (ld_acquire(p) >= target) return true;
-    const unsigned long long t0 = gtime();
-    for (unsigned n = 1;; ++n) {
-        if (ld_acquire(p) >= target) return true;
-        if ((n & 31) == 0) {
-            if (*(volatile int *)abort_flag) return false;
-            if (gtime() - t0 > kWaitTimeoutNs) {
-                atomicExch(abort_flag, 1);
-                atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
-                return false;
-            }
-        }
-        if (n > 64) __nanosleep(32);
-    }
 }
 
 template <class T> __device__ __forceinline__ T ldexp_t(T x, int n);
@@ -147,90 +129,246 @@ __global__ void k_step_counts(const GsJob<T> *__restrict__ jobs, int q, int nswe
     cnt[s] = n;
 }
 
-__device__ __forceinline__ int tiles_of(const int32_t *lvl_off, int i) {
-    return (lvl_off[i + 1] - lvl_off[i] + TILE - 1) / TILE;
+// ---------------------------------------------------------------- bulk copies into shared memory
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy; both addresses and the size are multiples of 16 bytes
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Wait until each counter reaches its target (target <= 0: no wait).  The
+// three loads go out together; bounded like wait_ge.
+__device__ bool wait_deps(const int32_t *p0, int t0, const int32_t *p1, int t1, const int32_t *p2, int t2,
+                          int *abort_flag, int *status) {
+    const unsigned long long tstart = gtime();
+    for (unsigned n = 0;; ++n) {
+        const int v0 = (t0 > 0) ? ld_acquire(p0) : 0;
+        const int v1 = (t1 > 0) ? ld_acquire(p1) : 0;
+        const int v2 = (t2 > 0) ? ld_acquire(p2) : 0;
+        if (v0 >= t0 && v1 >= t1 && v2 >= t2) return true;
+        if ((n & 31) == 31) {
+            if (*(volatile int *)abort_flag) return false;
+            if (gtime() - tstart > kWaitTimeoutNs) {
+                atomicExch(abort_flag, 1);
+                atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+                return false;
+            }
+        }
+        if (n > 64) __nanosleep(32);
+    }
+}
+
+constexpr int kCW = 8;                        // consumer warps per CTA
+constexpr int kThreads = 32 * (kCW + 1);      // + one producer warp
+constexpr int kVPT = TILE / (32 * kCW);       // positions per consumer thread
+constexpr int kEntPerV = 7;                   // staged entries per position (longer tiles read from global)
+static_assert(kVPT * 32 * kCW == TILE, "tile must split evenly over the consumer threads");
+
+// one staging buffer: the tile's row pointers, diagonal and rows, plus the
+// tile's facts written by the producer
+template <class T> struct alignas(128) Stage {
+    Ent<T> ent[TILE * kEntPerV + 4];
+    int grow[TILE + 12];
+    T diag[TILE + 8];
+    int start, count, lo, k, level, g0, d0, e0, fits, abort;
+};
+// every bulk-copy destination must start on a 16-byte boundary, in both stages
+static_assert(sizeof(Stage<float>) % 16 == 0 && sizeof(Stage<double>) % 16 == 0, "stage size");
+static_assert(offsetof(Stage<float>, grow) % 16 == 0 && offsetof(Stage<float>, diag) % 16 == 0, "stage layout");
+static_assert(offsetof(Stage<double>, grow) % 16 == 0 && offsetof(Stage<double>, diag) % 16 == 0, "stage layout");
+
+// tile number t of job J -> descriptor and step (t < J.ntickets)
 template <class T>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 4 : 2) k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nsweeps, int *abort_flag,
-                                             int *status) {
-    __shared__ int s_ok;
+__device__ __forceinline__ void lookup_tile(const GsJob<T> &J, int t, int nsweeps, int &scur, TileDesc &d, int &s) {
+    while (J.stepoff[scur + 1] <= t) ++scur;
+    s = scur;
+    int first, count;
+    step_range(J, s, nsweeps, first, count);
+    d = J.tiles[first + (t - J.stepoff[s])];
+}
+
+// bounded wait on an mbarrier phase
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (unsigned n = 1;; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((n & 63) == 0) {
+            if (gtime() - t0 > kWaitTimeoutNs) return false;
+        }
+    }
+}
+
+// Producer warp (one lane): for each of this CTA's tiles, in order, wait until
+// the staging buffer is free, stage the tile's row data with bulk copies,
+// look up the next tile, wait for the tile's three predecessor sets, then
+// release the buffer to the consumers.  Consumer warps: gather the neighbour
+// state, update, store, and count their warp into the set's counter.  Set
+// counters count warps: a set of nt tiles is complete for sweep k at
+// (k + 1) * nt * kCW.
+template <class T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
+    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nsweeps, int *abort_flag, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Stage<T> *stage = reinterpret_cast<Stage<T> *>(smem_raw);
+    __shared__ __align__(8) uint64_t full[2], empty[2];
     int q = 0;
     while (q + 1 < njobs && (int)blockIdx.x >= jobs[q + 1].cta0) ++q;
     const GsJob<T> &J = jobs[q];
-    const int nlev = J.nlev;
-    int scur = 0;
-    for (int t = (int)blockIdx.x - J.cta0; t < J.ntickets; t += J.ncta) {
-        // step of tile number t (tile numbers grow with the step)
-        while (J.stepoff[scur + 1] <= t) ++scur;
-        const int s = scur;
-        int first, count;
-        step_range(J, s, nsweeps, first, count);
-        const int2 tl = J.tiles[first + (t - J.stepoff[s])];
-        const int i = tl.x;
-        const int k = (s - i) >> 1;
-        const int lo_i = J.lvl_off[i];
-        const int r = tl.y + (int)threadIdx.x;
-        const bool act = r < J.lvl_off[i + 1];
-        // static row data, loaded before the wait
-        int b = 0, e = 0;
-        T dg = T(1);
-        int cols[kMaxDeg];
-        T wts[kMaxDeg];
-        if (act) {
-            b = __ldg(&J.grow[r]);
-            e = __ldg(&J.grow[r + 1]);
-            dg = __ldg(&J.diag[r]);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], kCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t_first = (int)blockIdx.x - J.cta0;
+    if (warp == 0) {
+        if (lane != 0) return;
+        constexpr int EA = 16 / (int)sizeof(Ent<T>);   // entries per 16 bytes
+        constexpr int DA = 16 / (int)sizeof(T);        // diagonal values per 16 bytes
+        int scur = 0;
+        TileDesc d;
+        int s = 0;
+        if (t_first < J.ntickets) lookup_tile(J, t_first, nsweeps, scur, d, s);
+        uint32_t eph[2] = {0u, 0u};
+        int j = 0;
+        for (int t = t_first; t < J.ntickets; t += J.ncta, ++j) {
+            const int b = j & 1;
+            Stage<T> &S = stage[b];
+            if (j >= 2) {
+                if (!mbar_wait_bounded(&empty[b], eph[b], abort_flag)) {
+                    atomicExch(abort_flag, 1);
+                    atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+                    return;   // consumers time out on their own bounded waits
+                }
+                eph[b] ^= 1u;
+            }
+            const int g0 = d.start & ~3, g1 = (d.start + d.count + 1 + 3) & ~3;
+            const int d0 = d.start & ~(DA - 1), d1 = (d.start + d.count + DA - 1) & ~(DA - 1);
+            const int e0 = d.eb & ~(EA - 1), e1 = (d.ee + EA - 1) & ~(EA - 1);
+            const int fits = (e1 - e0) <= TILE * kEntPerV + 4;
+            const uint32_t bg = 4u * (g1 - g0), bd = (uint32_t)sizeof(T) * (d1 - d0);
+            const uint32_t be = fits ? (uint32_t)sizeof(Ent<T>) * (e1 - e0) : 0u;
+            fence_proxy_async();
+            mbar_expect_tx_only(&full[b], bg + bd + be);
+            bulk_g2s(S.grow, J.grow + g0, bg, &full[b]);
+            bulk_g2s(S.diag, J.diag + d0, bd, &full[b]);
+            if (be) bulk_g2s(S.ent, J.gent + e0, be, &full[b]);
+            const int i = d.level, k = (s - d.level) >> 1;
+            S.start = d.start; S.count = d.count; S.lo = d.lo; S.k = k; S.level = i;
+            S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits;
+            // the next tile's descriptor, while the copies run
+            const TileDesc cur = d;
+            if (t + J.ncta < J.ntickets) lookup_tile(J, t + J.ncta, nsweeps, scur, d, s);
+            // predecessors: (k, i-1), (k-1, i), (k-1, i+1)
+            const int t0 = (i > 0) ? (k + 1) * cur.nt_prev * kCW : 0;
+            const int t1 = (k > 0) ? k * cur.nt_self * kCW : 0;
+            const int t2 = (k > 0) ? k * cur.nt_next * kCW : 0;
+            const bool ok = wait_deps(J.done + (i > 0 ? i - 1 : 0), t0, J.done + i, t1, J.done + i + 1, t2,
+                                      abort_flag, status);
+            S.abort = ok ? 0 : 1;
+            mbar_arrive(&full[b]);
+            if (!ok) return;
+        }
+        return;
+    }
+    // consumers
+    const int cw = warp - 1;
+    uint32_t fph[2] = {0u, 0u};
+    int j = 0;
+    for (int t = t_first; t < J.ntickets; t += J.ncta, ++j) {
+        const int b = j & 1;
+        Stage<T> &S = stage[b];
+        if (!mbar_wait_bounded(&full[b], fph[b], abort_flag)) {
+            if (lane == 0) {
+                atomicExch(abort_flag, 1);
+                atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+            }
+            return;
+        }
+        fph[b] ^= 1u;
+        if (S.abort) return;
+        const int start = S.start, count = S.count, lo = S.lo, k = S.k, level = S.level;
+        const int sg = S.g0, sd = S.d0, se = S.e0;
+        const Ent<T> *ent = S.fits ? S.ent : J.gent + se;
+        XVal<T> *Ucur = J.U[k & 1];
+        const XVal<T> *Uprv = J.U[(k & 1) ^ 1];
+        int rb[kVPT], re[kVPT];
+        XVal<T> u[kVPT][kMaxDeg];
+#pragma unroll
+        for (int v = 0; v < kVPT; ++v) {
+            const int p = v * 32 * kCW + cw * 32 + lane;
+            rb[v] = re[v] = 0;
+            if (p < count) {
+                const int r = start + p;
+                rb[v] = S.grow[r - sg] - se;
+                re[v] = S.grow[r - sg + 1] - se;
+            }
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) {
-                if (b + a < e) {
-                    cols[a] = __ldg(&J.gcol[b + a]);
-                    wts[a] = __ldg(&J.gw[b + a]);
+                if (rb[v] + a < re[v]) {
+                    const int c = ent[rb[v] + a].col;
+                    u[v][a] = ld_state((c < lo ? Ucur : Uprv) + c);
                 }
             }
         }
-        if (threadIdx.x == 0) {
-            bool ok = true;
-            if (i > 0) ok = wait_ge(&J.done[i - 1], (k + 1) * tiles_of(J.lvl_off, i - 1), abort_flag, status);
-            if (ok && k > 0) {
-                ok = wait_ge(&J.done[i], k * tiles_of(J.lvl_off, i), abort_flag, status);
-                if (ok && i + 1 < nlev) ok = wait_ge(&J.done[i + 1], k * tiles_of(J.lvl_off, i + 1), abort_flag, status);
-            }
-            s_ok = ok;
-        }
-        __syncthreads();
-        if (!s_ok) return;
-        if (act) {
-            XVal<T> *Ucur = J.U[k & 1];
-            const XVal<T> *Uprv = J.U[(k & 1) ^ 1];
-            XVal<T> u[kMaxDeg];
 #pragma unroll
-            for (int a = 0; a < kMaxDeg; ++a)
-                if (b + a < e) u[a] = ld_state((cols[a] < lo_i ? Ucur : Uprv) + cols[a]);
-            T acc = (i == 0) ? T(1) : T(0);  // u_0 = 1 on the sources
-            int eref = (i == 0) ? 0 : kZeroExp;
+        for (int v = 0; v < kVPT; ++v) {
+            const int p = v * 32 * kCW + cw * 32 + lane;
+            if (p >= count) continue;
+            const int r = start + p;
+            T acc = (lo == 0) ? T(1) : T(0);  // u_0 = 1 on the sources (D_0 starts at position 0)
+            int eref = (lo == 0) ? 0 : kZeroExp;
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) {
-                if (b + a < e && u[a].m != T(0)) {
-                    if (u[a].e > eref) {
-                        acc = ldexp_t<T>(acc, eref - u[a].e);
-                        eref = u[a].e;
+                if (rb[v] + a < re[v] && u[v][a].m != T(0)) {
+                    if (u[v][a].e > eref) {
+                        acc = ldexp_t<T>(acc, eref - u[v][a].e);
+                        eref = u[v][a].e;
                     }
-                    acc += wts[a] * ldexp_t<T>(u[a].m, u[a].e - eref);
+                    acc += ent[rb[v] + a].w * ldexp_t<T>(u[v][a].m, u[v][a].e - eref);
                 }
             }
-            for (int a = b + kMaxDeg; a < e; ++a) {  // long rows
-                const int c = __ldg(&J.gcol[a]);
-                const XVal<T> x = ld_state((c < lo_i ? Ucur : Uprv) + c);
-                if (x.m != T(0)) {
-                    if (x.e > eref) {
-                        acc = ldexp_t<T>(acc, eref - x.e);
-                        eref = x.e;
+            for (int a = rb[v] + kMaxDeg; a < re[v]; ++a) {  // long rows
+                const Ent<T> x = ent[a];
+                const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
+                if (w.m != T(0)) {
+                    if (w.e > eref) {
+                        acc = ldexp_t<T>(acc, eref - w.e);
+                        eref = w.e;
                     }
-                    acc += __ldg(&J.gw[a]) * ldexp_t<T>(x.m, x.e - eref);
+                    acc += x.w * ldexp_t<T>(w.m, w.e - eref);
                 }
             }
-            const T val = acc / dg;
+            const T val = acc / S.diag[r - sd];
             int ex = 0;
             const T mm = frexp_t<T>(val, &ex);
             XVal<T> out;
@@ -238,8 +376,11 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 4 : 2) k_gs(const GsJob
             out.e = (mm == T(0)) ? kZeroExp : ex + eref;
             Ucur[r] = out;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) red_release_add(&J.done[i], 1);
+        __syncwarp();
+        if (lane == 0) {
+            red_release_add(&J.done[level], 1);
+            mbar_arrive(&empty[b]);
+        }
     }
 }
 
@@ -259,7 +400,9 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     cudaStream_t st = c->stream;
     const int K = (int)ws.size();
     int per_sm = 0;
-    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs<T>, TILE, 0));
+    const size_t smem = 2 * sizeof(Stage<T>);
+    GH_CUDA(cudaFuncSetAttribute(k_gs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs<T>, kThreads, smem));
     if (per_sm < 1) { set_error("diffusion kernel does not fit on an SM"); return GH_EDEVICE; }
     const int grid = per_sm * c->num_sms;
     if (K > grid) { set_error("internal: more queries than resident CTAs in one diffusion launch"); return GH_EINVAL; }
@@ -283,13 +426,11 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
         cta += j.ncta;
         j.lvl_off = ptr<int32_t>(w.lvl_off);
         j.grow = ptr<int32_t>(w.grow);
-        j.gcol = ptr<int32_t>(w.gent);
-        j.gw = reinterpret_cast<const T *>(ptr<int32_t>(w.gent) + w.cap_nnz);
+        j.gent = ptr<Ent<T>>(w.gent);
         j.diag = ptr<T>(w.diag);
         j.ptile0 = ptr<int32_t>(w.ptile);
         j.ptile1 = ptr<int32_t>(w.ptile) + j.n_even + 1;
-        j.tiles = ptr<int2>(w.tiles);
-        int32_t *cnt = scratch + at;
+        j.tiles = ptr<TileDesc>(w.tiles);
         int32_t *soff = scratch + soff_total + at;
         at += (size_t)j.nsteps + 2;
         j.stepoff = soff;
@@ -318,7 +459,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     int *abort_flag = &c->bar_dev->abort;
     void *argv[] = {(void *)&djobs, (void *)&njobs, (void *)&sweeps, (void *)&abort_flag, (void *)&status};
     if (ev0) cudaEventRecord(ev0, st);
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_gs<T>, dim3(grid), dim3(TILE), argv, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_gs<T>, dim3(grid), dim3(kThreads), argv, smem, st);
     ++c->launches;
     if (ev1) cudaEventRecord(ev1, st);
     cudaFreeAsync(djobs, st);

@@ -59,6 +59,20 @@ template <class T> struct alignas(sizeof(T) == 4 ? 8 : 16) XVal {
     int e;
 };
 
+// One entry of a row of the level-ordered operator: neighbour position and
+// weight t * theta.  8 bytes in FP32, 16 in FP64.
+template <class T> struct alignas(sizeof(T) == 4 ? 8 : 16) Ent {
+    int col;
+    T w;
+};
+
+// One Gauss-Seidel tile: up to TILE consecutive queue positions of one set.
+struct alignas(16) TileDesc {
+    int level, start, count, lo;      // set index, first position, positions, first position of the set
+    int eb, ee, nt_prev, nt_self;     // entry range [eb, ee) of its rows; tiles in sets i-1 and i
+    int nt_next, pad0, pad1, pad2;    // tiles in set i+1 (0 past the last set)
+};
+
 // ---------------------------------------------------------------- mesh
 
 struct GridBarrier {
@@ -109,11 +123,11 @@ struct QueryWs {
     // breadth-first traversal
     DBuf level, parent, order, pos, key, lvl_off, meta;  // meta: [0] nlev [1] nreach [2] err
     // level-ordered Gauss-Seidel layout
-    DBuf grow;      // int32 [nv+1]
-    DBuf gent;      // {int32 col, T w} [2ne]
-    DBuf diag;      // T [nv]
-    DBuf tiles;     // int2 [nv + nv/TILE + 2] (level, start) sorted by (parity, level)
-    DBuf ptile;     // int32 [nv + 4] per-parity tile prefix over levels
+    DBuf grow;      // int32 [nv+1] (+ padding for aligned bulk copies)
+    DBuf gent;      // Ent<T> [2ne] (+ padding)
+    DBuf diag;      // T [nv] (+ padding)
+    DBuf tiles;     // TileDesc [nreach/TILE + nlev], sorted by (parity, level)
+    DBuf ptile;     // int32 [nv + 8] per-parity tile prefix over levels
     DBuf U0, U1;    // XVal<T> [nv] ping-pong state
     // stages
     DBuf h;         // T [nf*3]
@@ -142,7 +156,7 @@ struct MeshH {
 
 // ---------------------------------------------------------------- kernels (host launchers)
 
-constexpr int TILE = 256;  // vertices per Gauss-Seidel tile (one per thread)
+constexpr int TILE = 512;  // queue positions per Gauss-Seidel tile
 
 // scan.cu
 gh_status exclusive_scan_i32(Ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *total_host);

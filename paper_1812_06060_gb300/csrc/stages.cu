@@ -383,8 +383,8 @@ __global__ void k_jump(int64_t nv, const double *__restrict__ d_in, const int32_
 
 // per reached vertex r (queue order): (A - t L_c) u - u_0 in FP64
 template <class T>
-__global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restrict__ grow, const int32_t *__restrict__ gcol,
-                                                   const T *__restrict__ gw, const T *__restrict__ diag,
+__global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restrict__ grow, const Ent<T> *__restrict__ gent,
+                                                   const T *__restrict__ diag,
                                                    const int32_t *__restrict__ lvl_off, const XVal<T> *__restrict__ U,
                                                    double *part) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -394,8 +394,9 @@ __global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restr
         double uv = ldexp((double)ur.m, max(ur.e, -2000));
         double res = (double)diag[r] * uv;
         for (int a = grow[r]; a < grow[r + 1]; ++a) {
-            XVal<T> uc = U[gcol[a]];
-            res -= (double)gw[a] * ldexp((double)uc.m, max(uc.e, -2000));
+            Ent<T> en = gent[a];
+            XVal<T> uc = U[en.col];
+            res -= (double)en.w * ldexp((double)uc.m, max(uc.e, -2000));
         }
         if (r < lvl_off[1]) res -= 1.0;
         acc = res * res;
@@ -491,9 +492,7 @@ template <class T> gh_status heat_resid_t(Ctx *c, QueryWs &q) {
     unsigned nb = blocks_for(n, NT);
     double *part = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
-    const int32_t *gcol = ptr<int32_t>(q.gent);
-    const T *gw = reinterpret_cast<const T *>(gcol + q.cap_nnz);
-    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.grow), gcol, gw, ptr<T>(q.diag), ptr<int32_t>(q.lvl_off),
+    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.grow), ptr<Ent<T>>(q.gent), ptr<T>(q.diag), ptr<int32_t>(q.lvl_off),
                                        ptr<XVal<T>>(q.final_buf ? q.U1 : q.U0), part); ++c->launches;
     double *tmp = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * 2, st));
