@@ -196,6 +196,34 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out);
  * [4] integration, [5] the diffusion kernel launch alone. */
 gh_status gh_stage_times(gh_mesh mesh, double *ms6);
 
+/*
+ * Mean edge length (hbar of eq. DiffusionTime) of a mesh whose data the
+ * caller already holds on the device, with no device allocation at all.  The
+ * paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory, such as code running while a stream is captured
+ * into a CUDA graph, applications whose own allocator owns all device memory,
+ * or latency-critical paths where an allocation may synchronise the device.
+ *  V       device, float64 [nv][3] vertex positions.
+ *  edges   device, int32 [ne][2] vertex pairs, e.g. GH_DUMP_EDGES of a loaded
+ *          mesh; every index must be inside V.
+ *  ne      1 .. 536,870,912 edges (a fixed scratch of 8192 partial sums of
+ *          65,536 edges each); larger counts return GH_EINVAL.
+ *  out     device, float64 [1]: the mean edge length, the same two-level
+ *          fixed-order sum as gh_mesh_load uses.
+ *  stream  cudaStream_t (NULL = legacy default stream); the call only
+ *          enqueues two kernels and returns, out is ready when the stream
+ *          reaches that point.
+ * The partial sums live in one 64 KiB array in device memory that every GPU
+ * loading the library holds until the process exits.  All calls on a device
+ * share it, so calls whose kernels overlap on the GPU (different streams)
+ * race; each call overwrites every partial it reads, so nothing needs
+ * clearing.  The first call on a device looks the array's address up with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  Errors: GH_EINVAL (NULL or host pointer, ne out
+ * of range), GH_EDEVICE.
+ */
+gh_status gh_mean_edge_length_noalloc(const double *V, const int32_t *edges, int64_t ne, double *out, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *gh_last_error(void);
 

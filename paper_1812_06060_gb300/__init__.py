@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: 
 # symbols declared in include/geoheat.h
 EXPORTS = ["gh_params_default", "gh_version", "gh_ctx_create", "gh_ctx_destroy", "gh_ctx_set_stream", "gh_ctx_memory", "gh_ctx_stats",
            "gh_mesh_load", "gh_mesh_info", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
-           "gh_debug_dump", "gh_stage_times", "gh_last_error"]
+           "gh_debug_dump", "gh_stage_times", "gh_mean_edge_length_noalloc", "gh_last_error"]
 
 
 class GhParams(C.Structure):
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
     L.gh_debug_dump.argtypes = [P, I32, I32, P]
     L.gh_stage_times.restype = S
     L.gh_stage_times.argtypes = [P, C.POINTER(D)]
+    L.gh_mean_edge_length_noalloc.restype = S
+    L.gh_mean_edge_length_noalloc.argtypes = [P, P, I64, P, P]
     _lib = L
     return L
 
@@ -219,3 +221,12 @@ class Mesh:
 
 def gh_version() -> str:
     return lib().gh_version().decode()
+
+
+def mean_edge_length_noalloc(V, edges, out, stream=None):
+    """gh_mean_edge_length_noalloc: V (float64 [nv,3]), edges (int32 [ne,2]) and
+    out (float64 [1]) are device tensors; nothing is allocated on the device."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().gh_mean_edge_length_noalloc(_addr(V), _addr(edges), int(edges.shape[0]), _addr(out),
+                                             C.c_void_p(raw or 0)))
+    return out
