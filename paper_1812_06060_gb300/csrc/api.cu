@@ -116,7 +116,7 @@ static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int f
     // padded so 16-byte aligned bulk copies of any row window stay inside the buffers
     A(grow, 4 * (nv + 9)); A(gent, (nnz + 4) * (fp64 ? 16 : 8)); A(diag, es * (nv + 4));
     A(ptile, 4 * (nv + 8));
-    A(U0, xs * nv); A(U1, xs * nv);
+    A(U0, xs * (nv + 1)); A(U1, xs * (nv + 1));   // + the zero slot
     A(h, es * 3 * nf);
     if (form == GH_FORM_FACE) {
         A(g0, es * 3 * nf); A(g1, es * 3 * nf); A(l0, es * 9 * nf); A(l1, es * 9 * nf);

@@ -57,44 +57,83 @@ __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
     return total;
 }
 
+constexpr int kBfsChunks = 4;   // parents per thread whose rows stay in registers between the passes
+
+// Keys: a vertex discovered by the parent of rank r through the parent's
+// slot j holds (r << 32 | j); sources hold 0; undiscovered vertices hold the
+// maximum.  A discovered vertex always holds a key below every key a later
+// set offers, so the offers need no "already visited" test.
 __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
     const BfsArgs a = all[blockIdx.x];
     int lo = 0, hi = a.n0, nlev = 1;
     if (threadIdx.x == 0) a.lvl_off[0] = 0;
     while (true) {
-        // every parent offers its key to its undiscovered neighbours
-        for (int r = lo + threadIdx.x; r < hi; r += BT) {
-            int p = __ldcg(&a.order[r]);
-            int b = a.rowptr[p], e = a.rowptr[p + 1];
-            for (int j = b; j < e; ++j) {
-                int w = a.col[j];
-                if (__ldcg(&a.level[w]) < 0)
-                    atomicMin(&a.key[w], ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b));
+        const int n = hi - lo;
+        const int nchunk = (n + BT - 1) / BT;
+        int pp[kBfsChunks], rb[kBfsChunks], re[kBfsChunks];
+        // every parent offers its key to all its neighbours
+#pragma unroll
+        for (int c = 0; c < kBfsChunks; ++c) {
+            const int r = lo + c * BT + (int)threadIdx.x;
+            int p = -1, b = 0, e = 0;
+            if (c < nchunk && r < hi) {
+                p = __ldcg(&a.order[r]);
+                b = a.rowptr[p];
+                e = a.rowptr[p + 1];
+                for (int j = b; j < e; ++j)
+                    atomicMin(&a.key[a.col[j]], ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b));
+            }
+            pp[c] = p; rb[c] = b; re[c] = e;
+        }
+        for (int c = kBfsChunks; c < nchunk; ++c) {
+            const int r = lo + c * BT + (int)threadIdx.x;
+            if (r < hi) {
+                const int p = __ldcg(&a.order[r]);
+                const int b = a.rowptr[p], e = a.rowptr[p + 1];
+                for (int j = b; j < e; ++j)
+                    atomicMin(&a.key[a.col[j]], ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b));
             }
         }
         __syncthreads();
         // children in (parent rank, slot) order
         int base = hi;
-        for (int c0 = lo; c0 < hi; c0 += BT) {
-            int r = c0 + threadIdx.x;
-            int cnt = 0, p = -1, b = 0, e = 0;
-            if (r < hi) {
+        for (int c = 0; c < nchunk; ++c) {
+            const int r = lo + c * BT + (int)threadIdx.x;
+            int p = -1, b = 0, e = 0;
+            if (c < kBfsChunks) {
+#pragma unroll
+                for (int x = 0; x < kBfsChunks; ++x)
+                    if (x == c) { p = pp[x]; b = rb[x]; e = re[x]; }
+            } else if (r < hi) {
                 p = __ldcg(&a.order[r]);
                 b = a.rowptr[p];
                 e = a.rowptr[p + 1];
+            }
+            int cnt = 0;
+            unsigned mine_mask = 0;   // slots (up to 32) whose neighbour this parent discovered
+            if (r < hi) {
                 for (int j = b; j < e; ++j) {
-                    unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
-                    if (__ldcg(&a.key[a.col[j]]) == mine) ++cnt;
+                    const unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
+                    if (__ldcg(&a.key[a.col[j]]) == mine) {
+                        ++cnt;
+                        if (j - b < 32) mine_mask |= 1u << (j - b);
+                    }
                 }
             }
             int excl;
-            int total = bt_scan(cnt, excl);
+            const int total = bt_scan(cnt, excl);
             if (cnt) {
                 int at = base + excl;
                 for (int j = b; j < e; ++j) {
-                    int w = a.col[j];
-                    unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
-                    if (__ldcg(&a.key[w]) == mine) {
+                    bool is_child;
+                    if (j - b < 32) {
+                        is_child = (mine_mask >> (j - b)) & 1u;
+                    } else {
+                        const unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
+                        is_child = __ldcg(&a.key[a.col[j]]) == mine;
+                    }
+                    if (is_child) {
+                        const int w = a.col[j];
                         a.order[at++] = w;
                         a.level[w] = nlev;
                         a.parent[w] = p;
@@ -117,9 +156,13 @@ __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
     }
 }
 
-__global__ void k_seed(int32_t *level, const int32_t *order, int n0) {
+// sources: set 0, key 0
+__global__ void k_seed(int32_t *level, unsigned long long *key, const int32_t *order, int n0) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n0) level[order[i]] = 0;
+    if (i < n0) {
+        level[order[i]] = 0;
+        key[order[i]] = 0ull;
+    }
 }
 
 __global__ void k_pos(const int32_t *__restrict__ order, int n, int32_t *pos) {
@@ -136,7 +179,7 @@ __global__ void k_row_len(const int32_t *__restrict__ order, int n, const int32_
 }
 
 // row r of the level-ordered layout: neighbours renumbered to queue positions
-// with weight t*theta; diag = A_v + t * sum theta (FP64, then rounded)
+// with weight t*theta; idiag = 1 / (A_v + t * sum theta) (FP64, then rounded)
 template <class T>
 __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const int32_t *__restrict__ rowptr,
                               const int32_t *__restrict__ col, const int32_t *__restrict__ col_edge,
@@ -156,7 +199,7 @@ __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const in
         x.w = (T)(t * th);
         gent[o + (j - b)] = x;
     }
-    diag[r] = (T)(Av[v] + t * sum);
+    diag[r] = (T)(1.0 / (Av[v] + t * sum));
 }
 
 // tiles of at most TILE queue positions inside one set, listed set by set,
@@ -220,7 +263,7 @@ gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const st
         GH_CUDA(cudaMemsetAsync(w.parent.p, 0xff, sizeof(int32_t) * m.nv, st));
         GH_CUDA(cudaMemsetAsync(w.key.p, 0xff, sizeof(unsigned long long) * m.nv, st));
         GH_CUDA(cudaMemcpyAsync(w.order.p, src[q].data(), sizeof(int32_t) * src[q].size(), cudaMemcpyHostToDevice, st));
-        k_seed<<<blocks_for((int64_t)src[q].size(), 256), 256, 0, st>>>(ptr<int32_t>(w.level), ptr<int32_t>(w.order),
+        k_seed<<<blocks_for((int64_t)src[q].size(), 256), 256, 0, st>>>(ptr<int32_t>(w.level), ptr<unsigned long long>(w.key), ptr<int32_t>(w.order),
                                                                        (int)src[q].size()); ++c->launches;
         args[q] = BfsArgs{ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(w.level), ptr<int32_t>(w.parent),
                           ptr<int32_t>(w.order), ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off),

@@ -51,6 +51,8 @@ template <class T> struct GsJob {
     int n_even;            // number of even sets; ptile0[n_even] = first tile of the odd sets
     int ntickets;          // tiles over all steps
     int cta0, ncta;        // the CTAs serving this query
+    int zero_pos;          // a position that always holds the zero state (nreach)
+    int pad2;
     const int32_t *lvl_off;
     const int32_t *grow;
     const Ent<T> *gent;
@@ -59,7 +61,7 @@ template <class T> struct GsJob {
     const int32_t *ptile1;
     const TileDesc *tiles;
     const int32_t *stepoff;  // [nsteps + 1] first tile number of each step
-    int32_t *done;           // [nlev] finished tiles per set
+    int32_t *done;           // [nlev] tiles finished per set, over all sweeps
     XVal<T> *U[2];
 };
 
@@ -75,26 +77,68 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
     return v;
 }
 
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void red_release_add(int32_t *p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <class T> __device__ __forceinline__ T ldexp_t(T x, int n);
-template <> __device__ __forceinline__ float ldexp_t<float>(float x, int n) { return ldexpf(x, n); }
-template <> __device__ __forceinline__ double ldexp_t<double>(double x, int n) { return ldexp(x, n); }
-template <class T> __device__ __forceinline__ T frexp_t(T x, int *e);
-template <> __device__ __forceinline__ float frexp_t<float>(float x, int *e) { return frexpf(x, e); }
-template <> __device__ __forceinline__ double frexp_t<double>(double x, int *e) { return frexp(x, e); }
+// Exponent arithmetic on normalised mantissas (0.5 <= |m| < 1, or m = 0).
+// xscale(m, d) = m * 2^d for d <= 0, made by adding d to the exponent field;
+// a term more than 125 (FP64: 1021) binades below the largest term of a sum
+// is below the precision of the sum and is dropped (returns 0).
+__device__ __forceinline__ float xscale(float m, int d) {
+    return (d >= -125) ? __int_as_float(__float_as_int(m) + (d << 23)) : 0.0f;
+}
+__device__ __forceinline__ double xscale(double m, int d) {
+    return (d >= -1021) ? __longlong_as_double(__double_as_longlong(m) + ((long long)d << 52)) : 0.0;
+}
+// v * 2^eref -> (m, e) with m normalised (the role of frexp)
+__device__ __forceinline__ void xnorm(float v, int eref, float &m, int &e) {
+    int b = __float_as_int(v);
+    int ex = (b >> 23) & 0xff;
+    if (ex == 0) {
+        if ((b & 0x7fffffff) == 0) { m = 0.0f; e = kZeroExp; return; }
+        v *= 18446744073709551616.0f;  // subnormal: scale by 2^64 first
+        b = __float_as_int(v);
+        ex = ((b >> 23) & 0xff) - 64;
+    }
+    m = __int_as_float((b & 0x807fffff) | (126 << 23));
+    e = eref + (ex - 126);
+}
+__device__ __forceinline__ void xnorm(double v, int eref, double &m, int &e) {
+    long long b = __double_as_longlong(v);
+    int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) {
+        if ((b & 0x7fffffffffffffffll) == 0) { m = 0.0; e = kZeroExp; return; }
+        v *= 18446744073709551616.0;
+        b = __double_as_longlong(v);
+        ex = (int)((b >> 52) & 0x7ff) - 64;
+    }
+    m = __longlong_as_double((b & (long long)0x800fffffffffffffull) | (1022ll << 52));
+    e = eref + (ex - 1022);
+}
 
+// Neighbour state.  Plain (weak, L1-cached) loads: every value a tile reads
+// was stored before a release add on a set counter that the tile's producer
+// observed with an acquire load and passed on through the staging mbarrier
+// (release/acquire within the CTA), so the PTX memory model makes these
+// loads see it; L1 caching lets the 8 gathers of a warp share sectors.
 __device__ __forceinline__ XVal<float> ld_state(const XVal<float> *p) {
-    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    const float2 v = *reinterpret_cast<const float2 *>(p);
     XVal<float> x;
     x.m = v.x;
     x.e = __float_as_int(v.y);
     return x;
 }
 __device__ __forceinline__ XVal<double> ld_state(const XVal<double> *p) {
-    double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 v = *reinterpret_cast<const double2 *>(p);
     XVal<double> x;
     x.m = v.x;
     x.e = (int)__double_as_longlong(v.y);
@@ -161,16 +205,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Wait until each counter reaches its target (target <= 0: no wait).  The
-// three loads go out together; bounded like wait_ge.
-__device__ bool wait_deps(const int32_t *p0, int t0, const int32_t *p1, int t1, const int32_t *p2, int t2,
+// Wait until (k, i-1), (k-1, i) and (k-1, i+1) are complete: the set
+// counters (tiles finished, over all sweeps so far) reach their targets
+// (a target <= 0 means no wait).  The three counters are polled with relaxed
+// loads that go out together; once all are met one acquire fence orders the
+// tile's reads after the releases observed.  Bounded like every wait.
+__device__ bool wait_sets(const int32_t *p0, int t0, const int32_t *p1, int t1, const int32_t *p2, int t2,
                           int *abort_flag, int *status) {
     const unsigned long long tstart = gtime();
     for (unsigned n = 0;; ++n) {
-        const int v0 = (t0 > 0) ? ld_acquire(p0) : 0;
-        const int v1 = (t1 > 0) ? ld_acquire(p1) : 0;
-        const int v2 = (t2 > 0) ? ld_acquire(p2) : 0;
-        if (v0 >= t0 && v1 >= t1 && v2 >= t2) return true;
+        const int v0 = (t0 > 0) ? ld_relaxed(p0) : 0;
+        const int v1 = (t1 > 0) ? ld_relaxed(p1) : 0;
+        const int v2 = (t2 > 0) ? ld_relaxed(p2) : 0;
+        if (v0 >= t0 && v1 >= t1 && v2 >= t2) {
+            fence_acquire();
+            return true;
+        }
         if ((n & 31) == 31) {
             if (*(volatile int *)abort_flag) return false;
             if (gtime() - tstart > kWaitTimeoutNs) {
@@ -195,7 +245,7 @@ template <class T> struct alignas(128) Stage {
     Ent<T> ent[TILE * kEntPerV + 4];
     int grow[TILE + 12];
     T diag[TILE + 8];
-    int start, count, lo, k, level, g0, d0, e0, fits, abort;
+    int start, count, lo, k, level, g0, d0, e0, fits, abort, finished;
 };
 // every bulk-copy destination must start on a 16-byte boundary, in both stages
 static_assert(sizeof(Stage<float>) % 16 == 0 && sizeof(Stage<double>) % 16 == 0, "stage size");
@@ -204,12 +254,14 @@ static_assert(offsetof(Stage<double>, grow) % 16 == 0 && offsetof(Stage<double>,
 
 // tile number t of job J -> descriptor and step (t < J.ntickets)
 template <class T>
-__device__ __forceinline__ void lookup_tile(const GsJob<T> &J, int t, int nsweeps, int &scur, TileDesc &d, int &s) {
+__device__ __forceinline__ void lookup_tile(const GsJob<T> &J, int t, int nsweeps, int &scur, TileDesc &d, int &s,
+                                            int &tile) {
     while (J.stepoff[scur + 1] <= t) ++scur;
     s = scur;
     int first, count;
     step_range(J, s, nsweeps, first, count);
-    d = J.tiles[first + (t - J.stepoff[s])];
+    tile = first + (t - J.stepoff[s]);
+    d = J.tiles[tile];
 }
 
 // bounded wait on an mbarrier phase
@@ -228,9 +280,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // the staging buffer is free, stage the tile's row data with bulk copies,
 // look up the next tile, wait for the tile's three predecessor sets, then
 // release the buffer to the consumers.  Consumer warps: gather the neighbour
-// state, update, store, and count their warp into the set's counter.  Set
-// counters count warps: a set of nt tiles is complete for sweep k at
-// (k + 1) * nt * kCW.
+// state, update and store; the last warp of the tile to finish adds one to
+// the set's counter with a release add, so a set of nt tiles is complete for
+// sweep k once its counter reaches (k + 1) * nt.
 template <class T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
     k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nsweeps, int *abort_flag, int *status) {
@@ -244,6 +296,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], kCW);
+            stage[b].finished = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -251,52 +304,73 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t_first = (int)blockIdx.x - J.cta0;
     if (warp == 0) {
-        if (lane != 0) return;
+        // Producer warp.  Lane l looks up the l-th of the next 32 tiles of this
+        // CTA (one parallel lookup per 32 tiles); lane 0 then stages, waits and
+        // releases them one by one.
         constexpr int EA = 16 / (int)sizeof(Ent<T>);   // entries per 16 bytes
         constexpr int DA = 16 / (int)sizeof(T);        // diagonal values per 16 bytes
         int scur = 0;
-        TileDesc d;
-        int s = 0;
-        if (t_first < J.ntickets) lookup_tile(J, t_first, nsweeps, scur, d, s);
         uint32_t eph[2] = {0u, 0u};
         int j = 0;
-        for (int t = t_first; t < J.ntickets; t += J.ncta, ++j) {
-            const int b = j & 1;
-            Stage<T> &S = stage[b];
-            if (j >= 2) {
-                if (!mbar_wait_bounded(&empty[b], eph[b], abort_flag)) {
-                    atomicExch(abort_flag, 1);
-                    atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
-                    return;   // consumers time out on their own bounded waits
+        for (int base = t_first; base < J.ntickets; base += 32 * J.ncta) {
+            const int tl = base + lane * J.ncta;
+            TileDesc dl{};
+            int sl = 0, tidl = 0;
+            if (tl < J.ntickets) lookup_tile(J, tl, nsweeps, scur, dl, sl, tidl);
+            const int nwin = min(32, (J.ntickets - base + J.ncta - 1) / J.ncta);
+            for (int w = 0; w < nwin; ++w, ++j) {
+                TileDesc d;
+                d.level = __shfl_sync(0xffffffffu, dl.level, w);
+                d.start = __shfl_sync(0xffffffffu, dl.start, w);
+                d.count = __shfl_sync(0xffffffffu, dl.count, w);
+                d.lo = __shfl_sync(0xffffffffu, dl.lo, w);
+                d.eb = __shfl_sync(0xffffffffu, dl.eb, w);
+                d.ee = __shfl_sync(0xffffffffu, dl.ee, w);
+                d.nt_prev = __shfl_sync(0xffffffffu, dl.nt_prev, w);
+                d.nt_self = __shfl_sync(0xffffffffu, dl.nt_self, w);
+                d.nt_next = __shfl_sync(0xffffffffu, dl.nt_next, w);
+                const int s = __shfl_sync(0xffffffffu, sl, w);
+                const int tile = __shfl_sync(0xffffffffu, tidl, w);
+                int ok = 1;
+                if (lane == 0) {
+                    const int b = j & 1;
+                    Stage<T> &S = stage[b];
+                    if (j >= 2) {
+                        if (!mbar_wait_bounded(&empty[b], eph[b], abort_flag)) {
+                            atomicExch(abort_flag, 1);
+                            atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+                            ok = 0;   // consumers time out on their own bounded waits
+                        }
+                        eph[b] ^= 1u;
+                    }
+                    if (ok) {
+                        const int g0 = d.start & ~3, g1 = (d.start + d.count + 1 + 3) & ~3;
+                        const int d0 = d.start & ~(DA - 1), d1 = (d.start + d.count + DA - 1) & ~(DA - 1);
+                        const int e0 = d.eb & ~(EA - 1), e1 = (d.ee + EA - 1) & ~(EA - 1);
+                        const int fits = (e1 - e0) <= TILE * kEntPerV + 4;
+                        const uint32_t bg = 4u * (g1 - g0), bd = (uint32_t)sizeof(T) * (d1 - d0);
+                        const uint32_t be = fits ? (uint32_t)sizeof(Ent<T>) * (e1 - e0) : 0u;
+                        fence_proxy_async();
+                        mbar_expect_tx_only(&full[b], bg + bd + be);
+                        bulk_g2s(S.grow, J.grow + g0, bg, &full[b]);
+                        bulk_g2s(S.diag, J.diag + d0, bd, &full[b]);
+                        if (be) bulk_g2s(S.ent, J.gent + e0, be, &full[b]);
+                        const int i = d.level, k = (s - d.level) >> 1;
+                        S.start = d.start; S.count = d.count; S.lo = d.lo; S.k = k; S.level = i;
+                        S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits;
+                        // predecessors: (k, i-1), (k-1, i), (k-1, i+1)
+                        const int t0 = (i > 0) ? (k + 1) * d.nt_prev : 0;
+                        const int t1 = (k > 0) ? k * d.nt_self : 0;
+                        const int t2 = (k > 0) ? k * d.nt_next : 0;
+                        ok = wait_sets(J.done + (i > 0 ? i - 1 : 0), t0, J.done + i, t1, J.done + i + 1, t2,
+                                       abort_flag, status) ? 1 : 0;
+                        S.abort = ok ? 0 : 1;
+                        mbar_arrive(&full[b]);
+                    }
                 }
-                eph[b] ^= 1u;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) return;
             }
-            const int g0 = d.start & ~3, g1 = (d.start + d.count + 1 + 3) & ~3;
-            const int d0 = d.start & ~(DA - 1), d1 = (d.start + d.count + DA - 1) & ~(DA - 1);
-            const int e0 = d.eb & ~(EA - 1), e1 = (d.ee + EA - 1) & ~(EA - 1);
-            const int fits = (e1 - e0) <= TILE * kEntPerV + 4;
-            const uint32_t bg = 4u * (g1 - g0), bd = (uint32_t)sizeof(T) * (d1 - d0);
-            const uint32_t be = fits ? (uint32_t)sizeof(Ent<T>) * (e1 - e0) : 0u;
-            fence_proxy_async();
-            mbar_expect_tx_only(&full[b], bg + bd + be);
-            bulk_g2s(S.grow, J.grow + g0, bg, &full[b]);
-            bulk_g2s(S.diag, J.diag + d0, bd, &full[b]);
-            if (be) bulk_g2s(S.ent, J.gent + e0, be, &full[b]);
-            const int i = d.level, k = (s - d.level) >> 1;
-            S.start = d.start; S.count = d.count; S.lo = d.lo; S.k = k; S.level = i;
-            S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits;
-            // the next tile's descriptor, while the copies run
-            const TileDesc cur = d;
-            if (t + J.ncta < J.ntickets) lookup_tile(J, t + J.ncta, nsweeps, scur, d, s);
-            // predecessors: (k, i-1), (k-1, i), (k-1, i+1)
-            const int t0 = (i > 0) ? (k + 1) * cur.nt_prev * kCW : 0;
-            const int t1 = (k > 0) ? k * cur.nt_self * kCW : 0;
-            const int t2 = (k > 0) ? k * cur.nt_next * kCW : 0;
-            const bool ok = wait_deps(J.done + (i > 0 ? i - 1 : 0), t0, J.done + i, t1, J.done + i + 1, t2,
-                                      abort_flag, status);
-            S.abort = ok ? 0 : 1;
-            mbar_arrive(&full[b]);
-            if (!ok) return;
         }
         return;
     }
@@ -318,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         if (S.abort) return;
         const int start = S.start, count = S.count, lo = S.lo, k = S.k, level = S.level;
         const int sg = S.g0, sd = S.d0, se = S.e0;
-        const Ent<T> *ent = S.fits ? S.ent : J.gent + se;
+        const bool fits = S.fits != 0;
         XVal<T> *Ucur = J.U[k & 1];
         const XVal<T> *Uprv = J.U[(k & 1) ^ 1];
         int rb[kVPT], re[kVPT];
@@ -332,12 +406,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                 rb[v] = S.grow[r - sg] - se;
                 re[v] = S.grow[r - sg + 1] - se;
             }
+            // all gathers of the thread go out together; a missing entry reads
+            // the zero state kept at position nreach
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) {
-                if (rb[v] + a < re[v]) {
-                    const int c = ent[rb[v] + a].col;
-                    u[v][a] = ld_state((c < lo ? Ucur : Uprv) + c);
-                }
+                int c = J.zero_pos;
+                if (rb[v] + a < re[v]) c = fits ? S.ent[rb[v] + a].col : J.gent[se + rb[v] + a].col;
+                u[v][a] = ld_state((c < lo ? Ucur : Uprv) + c);
             }
         }
 #pragma unroll
@@ -345,40 +420,41 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
             const int p = v * 32 * kCW + cw * 32 + lane;
             if (p >= count) continue;
             const int r = start + p;
-            T acc = (lo == 0) ? T(1) : T(0);  // u_0 = 1 on the sources (D_0 starts at position 0)
-            int eref = (lo == 0) ? 0 : kZeroExp;
+            // the sum is formed relative to its largest exponent (u_0 = 1 = 0.5 * 2^1 on the sources)
+            int eref = (lo == 0) ? 1 : kZeroExp;   // zero states carry kZeroExp: no test needed
+#pragma unroll
+            for (int a = 0; a < kMaxDeg; ++a) eref = max(eref, u[v][a].e);
+            for (int a = rb[v] + kMaxDeg; a < re[v]; ++a) {  // long rows
+                const Ent<T> x = fits ? S.ent[a] : J.gent[se + a];
+                const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
+                if (w.m != T(0)) eref = max(eref, w.e);
+            }
+            T acc = (lo == 0) ? xscale(T(0.5), 1 - eref) : T(0);
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) {
-                if (rb[v] + a < re[v] && u[v][a].m != T(0)) {
-                    if (u[v][a].e > eref) {
-                        acc = ldexp_t<T>(acc, eref - u[v][a].e);
-                        eref = u[v][a].e;
-                    }
-                    acc += ent[rb[v] + a].w * ldexp_t<T>(u[v][a].m, u[v][a].e - eref);
-                }
+                T w = T(0);
+                if (rb[v] + a < re[v]) w = fits ? S.ent[rb[v] + a].w : J.gent[se + rb[v] + a].w;
+                acc += w * xscale(u[v][a].m, u[v][a].e - eref);
             }
-            for (int a = rb[v] + kMaxDeg; a < re[v]; ++a) {  // long rows
-                const Ent<T> x = ent[a];
+            for (int a = rb[v] + kMaxDeg; a < re[v]; ++a) {
+                const Ent<T> x = fits ? S.ent[a] : J.gent[se + a];
                 const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
-                if (w.m != T(0)) {
-                    if (w.e > eref) {
-                        acc = ldexp_t<T>(acc, eref - w.e);
-                        eref = w.e;
-                    }
-                    acc += x.w * ldexp_t<T>(w.m, w.e - eref);
-                }
+                acc += x.w * xscale(w.m, w.e - eref);
             }
-            const T val = acc / S.diag[r - sd];
-            int ex = 0;
-            const T mm = frexp_t<T>(val, &ex);
             XVal<T> out;
-            out.m = mm;
-            out.e = (mm == T(0)) ? kZeroExp : ex + eref;
+            xnorm(acc * S.diag[r - sd], eref, out.m, out.e);   // diag holds 1 / (A_v + t sum theta)
             Ucur[r] = out;
         }
         __syncwarp();
         if (lane == 0) {
-            red_release_add(&J.done[level], 1);
+            // the last warp of the tile publishes it with one release add
+            __threadfence_block();
+            const int before = atomicAdd(&S.finished, 1);
+            if (before == kCW - 1) {
+                S.finished = 0;
+                __threadfence_block();
+                red_release_add(&J.done[level], 1);
+            }
             mbar_arrive(&empty[b]);
         }
     }
@@ -437,6 +513,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
         j.done = ptr<int32_t>(w.n1);
         j.U[0] = ptr<XVal<T>>(w.U0);
         j.U[1] = ptr<XVal<T>>(w.U1);
+        j.zero_pos = w.nreach;
         jobs[q] = j;
         w.final_buf = (sweeps - 1) & 1;
     }
@@ -444,7 +521,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     std::vector<int32_t> ntick(K);
     for (int q = 0; q < K; ++q) {
         QueryWs &w = *ws[q];
-        k_zero_state<T><<<blocks_for(w.nreach, 256), 256, 0, st>>>(jobs[q].U[0], jobs[q].U[1], w.nreach); ++c->launches;
+        k_zero_state<T><<<blocks_for(w.nreach + 1, 256), 256, 0, st>>>(jobs[q].U[0], jobs[q].U[1], w.nreach + 1); ++c->launches;
         GH_CUDA(cudaMemsetAsync(jobs[q].done, 0, sizeof(int32_t) * (w.nlev + 1), st));
         int32_t *cnt = const_cast<int32_t *>(jobs[q].stepoff) - soff_total;
         k_step_counts<T><<<blocks_for(jobs[q].nsteps, 256), 256, 0, st>>>(djobs, q, sweeps, cnt); ++c->launches;

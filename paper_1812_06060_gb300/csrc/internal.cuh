@@ -125,7 +125,7 @@ struct QueryWs {
     // level-ordered Gauss-Seidel layout
     DBuf grow;      // int32 [nv+1] (+ padding for aligned bulk copies)
     DBuf gent;      // Ent<T> [2ne] (+ padding)
-    DBuf diag;      // T [nv] (+ padding)
+    DBuf diag;      // T [nv] (+ padding): 1 / (A_v + t sum theta)
     DBuf tiles;     // TileDesc [nreach/TILE + nlev], sorted by (parity, level)
     DBuf ptile;     // int32 [nv + 8] per-parity tile prefix over levels
     DBuf U0, U1;    // XVal<T> [nv] ping-pong state

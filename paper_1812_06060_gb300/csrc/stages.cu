@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restr
     if (r < n) {
         XVal<T> ur = U[r];
         double uv = ldexp((double)ur.m, max(ur.e, -2000));
-        double res = (double)diag[r] * uv;
+        double res = uv / (double)diag[r];   // diag holds 1 / (A_v + t sum theta)
         for (int a = grow[r]; a < grow[r + 1]; ++a) {
             Ent<T> en = gent[a];
             XVal<T> uc = U[en.col];
