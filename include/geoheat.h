@@ -132,6 +132,7 @@ gh_status gh_mesh_load(gh_ctx ctx, const double *V, int64_t nv, const int32_t *F
  * pointer may be NULL. */
 gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, double *mean_edge_len);
 
+/* Frees the mesh; GH_EBUSY while serving requests on it are in flight. */
 gh_status gh_mesh_free(gh_mesh mesh);
 
 /*
@@ -155,6 +156,32 @@ gh_status gh_solve(gh_mesh mesh, const int32_t *src, int32_t nsrc, const gh_para
  */
 gh_status gh_solve_batch(gh_mesh mesh, const int32_t *src_off, const int32_t *src, int32_t K,
                          const gh_params *params, double *d_out);
+
+/*
+ * Serving with continuous batching.  gh_submit queues one source set on a
+ * loaded mesh and returns at once with a request id.  Worker threads of the
+ * context (each with its own CUDA stream and workspaces) admit pending
+ * requests as memory and batch slots free up, in arrival order, grouping
+ * those that share the mesh and parameters, and run each group as one batch
+ * (one breadth-first launch and one diffusion launch for all of it); requests
+ * that arrive while others run join the next batch, and the workers' batches
+ * overlap on the device.  A request's distances equal those of gh_solve with
+ * the same arguments.  gh_submit, gh_poll and gh_wait are thread-safe.
+ *
+ * gh_serve_config: number of workers (1..8, default 2) and the batch limit
+ * (1..256, default 32); only before the first gh_submit on the context.
+ * gh_submit: src is host or device int32 [nsrc] (copied); errors as gh_solve.
+ * gh_poll: *done = 1 once the request has finished (successfully or not).
+ * gh_wait: waits up to timeout_us microseconds (< 0: no limit), then copies
+ *   the distances (float64 [nv], host or device) to d_out and forgets the
+ *   request; GH_ETIMEOUT leaves it pending, GH_ENOTFOUND for unknown ids, and
+ *   a failed request returns its error here.
+ * A mesh cannot be freed while it has requests in flight (GH_EBUSY).
+ */
+gh_status gh_serve_config(gh_ctx ctx, int32_t workers, int32_t max_batch);
+gh_status gh_submit(gh_ctx ctx, gh_mesh mesh, const int32_t *src, int32_t nsrc, const gh_params *params, gh_req *out);
+gh_status gh_poll(gh_ctx ctx, gh_req req, int *done);
+gh_status gh_wait(gh_ctx ctx, gh_req req, double *d_out, int64_t timeout_us);
 
 /*
  * Intermediates of query `query` of the last gh_solve / gh_solve_batch on

@@ -34,7 +34,8 @@ STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: 
 # symbols declared in include/geoheat.h
 EXPORTS = ["gh_params_default", "gh_version", "gh_ctx_create", "gh_ctx_destroy", "gh_ctx_set_stream", "gh_ctx_memory", "gh_ctx_stats",
            "gh_mesh_load", "gh_mesh_info", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
-           "gh_debug_dump", "gh_stage_times", "gh_mean_edge_length_noalloc", "gh_last_error"]
+           "gh_debug_dump", "gh_stage_times", "gh_mean_edge_length_noalloc", "gh_serve_config", "gh_submit", "gh_poll",
+           "gh_wait", "gh_last_error"]
 
 
 class GhParams(C.Structure):
@@ -92,6 +93,14 @@ def load_library(path: str = LIB_PATH):
     L.gh_debug_dump.argtypes = [P, I32, I32, P]
     L.gh_stage_times.restype = S
     L.gh_stage_times.argtypes = [P, C.POINTER(D)]
+    L.gh_serve_config.restype = S
+    L.gh_serve_config.argtypes = [P, I32, I32]
+    L.gh_submit.restype = S
+    L.gh_submit.argtypes = [P, P, P, I32, C.POINTER(GhParams), C.POINTER(C.c_uint64)]
+    L.gh_poll.restype = S
+    L.gh_poll.argtypes = [P, C.c_uint64, C.POINTER(C.c_int)]
+    L.gh_wait.restype = S
+    L.gh_wait.argtypes = [P, C.c_uint64, P, I64]
     L.gh_mean_edge_length_noalloc.restype = S
     L.gh_mean_edge_length_noalloc.argtypes = [P, P, I64, P, P]
     _lib = L
@@ -144,6 +153,26 @@ class Context:
         n = C.c_size_t()
         _check(lib().gh_ctx_memory(self.handle, C.byref(n)))
         return n.value
+
+    def serve_config(self, workers: int = 2, max_batch: int = 32):
+        _check(lib().gh_serve_config(self.handle, workers, max_batch))
+
+    def submit(self, mesh: "Mesh", sources, prm: GhParams) -> int:
+        """Queue one source set (gh_submit); returns the request id."""
+        src = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)
+        rid = C.c_uint64()
+        _check(lib().gh_submit(self.handle, mesh.handle, _addr(src), int(src.shape[0]), C.byref(prm), C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = C.c_int()
+        _check(lib().gh_poll(self.handle, rid, C.byref(done)))
+        return bool(done.value)
+
+    def wait(self, rid: int, out, timeout_us: int = -1):
+        """Wait for a request and copy its distances into ``out`` (gh_wait)."""
+        _check(lib().gh_wait(self.handle, rid, _addr(out), timeout_us))
+        return out
 
     def kernel_launches(self) -> int:
         n = C.c_uint64()

@@ -9,10 +9,19 @@
 
 #include "internal.cuh"
 
+namespace gh {
+struct Engine;
+void engine_stop(Engine *e);
+}
+
 struct gh_ctx_s {
     gh::Ctx c;
+    gh::Shared shared;
     std::mutex mu;
     std::vector<gh_mesh_s *> meshes;
+    gh::Engine *engine = nullptr;   // serving workers, started by the first gh_submit
+    std::mutex engine_mu;           // guards the start of the serving workers
+    int serve_workers = 2, serve_max_batch = 32;
 };
 
 struct gh_mesh_s {
@@ -36,26 +45,30 @@ gh_status dalloc(Ctx *c, DBuf &b, size_t bytes) {
     if (b.p && b.bytes >= bytes) return GH_OK;
     dfree(c, b);
     if (bytes == 0) bytes = 16;
-    if (c->budget && c->in_use + bytes > c->budget) {
-        set_error("device memory budget of the context exceeded (" + std::to_string(c->in_use + bytes) + " > " +
-                  std::to_string(c->budget) + " bytes)");
-        return GH_ENOMEM;
-    }
+    Shared *sh = c->shared;
+    size_t cur = sh->in_use.load();
+    do {
+        if (sh->budget && cur + bytes > sh->budget) {
+            set_error("device memory budget of the context exceeded (" + std::to_string(cur + bytes) + " > " +
+                      std::to_string(sh->budget) + " bytes)");
+            return GH_ENOMEM;
+        }
+    } while (!sh->in_use.compare_exchange_weak(cur, cur + bytes));
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         b.p = nullptr;
+        sh->in_use -= bytes;
         (void)cudaGetLastError();
         return cuda_fail(e, "cudaMalloc");
     }
     b.bytes = bytes;
-    c->in_use += bytes;
     return GH_OK;
 }
 
 void dfree(Ctx *c, DBuf &b) {
     if (b.p) {
         cudaFree(b.p);
-        c->in_use -= b.bytes;
+        c->shared->in_use -= b.bytes;
     }
     b.p = nullptr;
     b.bytes = 0;
@@ -78,7 +91,7 @@ gh_status check_status(Ctx *c, const char *stage) {
     }
 }
 
-static bool is_device_ptr(const void *p) {
+bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -89,7 +102,7 @@ static bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static void free_ws(Ctx *c, QueryWs *w) {
+void free_ws(Ctx *c, QueryWs *w) {
     DBuf *all[] = {&w->level, &w->parent, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->grow, &w->gent,
                    &w->diag, &w->tiles, &w->ptile, &w->U0, &w->U1, &w->h, &w->g0, &w->g1, &w->l0, &w->l1, &w->z,
                    &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1};
@@ -129,7 +142,7 @@ static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int f
     return GH_OK;
 }
 
-static gh_status validate_params(const gh_params *p) {
+gh_status validate_params(const gh_params *p) {
     if (!p) { set_error("params is NULL"); return GH_EINVAL; }
     if (p->gs_sweeps < 1) { set_error("gs_sweeps must be >= 1"); return GH_EINVAL; }
     if (p->admm_iters < 0) { set_error("admm_iters must be >= 0"); return GH_EINVAL; }
@@ -140,7 +153,7 @@ static gh_status validate_params(const gh_params *p) {
 }
 
 // bytes one query's workspace needs
-static size_t ws_bytes(const DevMesh &m, int fp64, int form) {
+size_t ws_bytes(const DevMesh &m, int fp64, int form) {
     const size_t es = fp64 ? 8 : 4, xs = fp64 ? 16 : 8;
     size_t nv = m.nv, nf = m.nf, ne = m.ne;
     size_t b = nv * (4 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) + es * 3 * nf;
@@ -149,33 +162,32 @@ static size_t ws_bytes(const DevMesh &m, int fp64, int form) {
 }
 
 // Run queries src[0..K) through the whole path; d_out (device) gets K x nv.
-static gh_status solve_impl(gh_mesh_s *mh, const std::vector<std::vector<int32_t>> &src, const gh_params *p,
-                            double *d_out_dev) {
-    Ctx *c = &mh->ctx->c;
-    DevMesh &m = mh->h.m;
+gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
+                     const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k) {
     const int K = (int)src.size();
     const double t = (p->t > 0) ? p->t : p->m * m.hbar * m.hbar;
     // queries per pass: as many as the budget (or 80% of free memory) allows, at most 64
     size_t per = ws_bytes(m, p->fp64, p->form);
     size_t avail;
-    if (c->budget) {
-        avail = c->budget > c->in_use ? c->budget - c->in_use : 0;
+    if (c->shared->budget) {
+        size_t used = c->shared->in_use.load();
+        avail = c->shared->budget > used ? c->shared->budget - used : 0;
     } else {
         size_t fr = 0, tot = 0;
         GH_CUDA(cudaMemGetInfo(&fr, &tot));
         avail = (size_t)(0.8 * (double)fr);
     }
-    for (QueryWs *w : mh->h.ws) avail += w->level.p ? per : 0;  // workspaces already held are reusable
+    for (QueryWs *w : pool) avail += w->level.p ? per : 0;  // workspaces already held are reusable
     int chunk = (int)std::min<size_t>(64, std::max<size_t>(1, avail / per));
     chunk = std::min(chunk, K);
-    while ((int)mh->h.ws.size() < chunk) mh->h.ws.push_back(new QueryWs());
+    while ((int)pool.size() < chunk) pool.push_back(new QueryWs());
     cudaEvent_t ev[8];
     for (auto &e : ev) GH_CUDA(cudaEventCreate(&e));
     double ms[5] = {0, 0, 0, 0, 0}, gs_ms = 0.0;
     gh_status s = GH_OK;
     for (int q0 = 0; q0 < K && s == GH_OK; q0 += chunk) {
         int kq = std::min(chunk, K - q0);
-        std::vector<QueryWs *> ws(mh->h.ws.begin(), mh->h.ws.begin() + kq);
+        std::vector<QueryWs *> ws(pool.begin(), pool.begin() + kq);
         for (int q = 0; q < kq && s == GH_OK; ++q) {
             s = ensure_ws(c, m, *ws[q], p->fp64, p->form, p->admm_iters);
             ws[q]->diagnostics = p->diagnostics;
@@ -216,15 +228,30 @@ static gh_status solve_impl(gh_mesh_s *mh, const std::vector<std::vector<int32_t
     }
     for (auto &e : ev) cudaEventDestroy(e);
     if (s == GH_OK) {
-        mh->h.last_k = std::min(K, chunk);
-        std::copy(ms, ms + 5, mh->h.stage_ms);
-        mh->h.gs_kernel_ms = gs_ms;
+        if (last_k) *last_k = std::min(K, chunk);
+        if (stage_ms6) {
+            std::copy(ms, ms + 5, stage_ms6);
+            stage_ms6[5] = gs_ms;
+        }
+    }
+    return s;
+}
+
+static gh_status solve_impl(gh_mesh_s *mh, const std::vector<std::vector<int32_t>> &src, const gh_params *p,
+                            double *d_out_dev) {
+    double ms6[6];
+    int lk = 0;
+    gh_status s = solve_core(&mh->ctx->c, mh->h.m, mh->h.ws, src, p, d_out_dev, ms6, &lk);
+    if (s == GH_OK) {
+        mh->h.last_k = lk;
+        std::copy(ms6, ms6 + 5, mh->h.stage_ms);
+        mh->h.gs_kernel_ms = ms6[5];
     }
     return s;
 }
 
 // sources of one set, validated, sorted and de-duplicated
-static gh_status prep_sources(const int32_t *src, int32_t nsrc, int64_t nv, std::vector<int32_t> &out) {
+gh_status prep_sources(const int32_t *src, int32_t nsrc, int64_t nv, std::vector<int32_t> &out) {
     if (!src || nsrc < 1) { set_error("a source set needs at least one vertex"); return GH_EINVAL; }
     out.resize(nsrc);
     if (is_device_ptr(src)) {
@@ -260,7 +287,30 @@ static gh_status solve_to(gh_mesh_s *mh, const std::vector<std::vector<int32_t>>
 
 using namespace gh;
 
+// accessors used by the serving engine (serve.cu)
+gh::Ctx *gh_ctx_launcher(gh_ctx_s *ctx) { return &ctx->c; }
+gh::Shared *gh_ctx_shared(gh_ctx_s *ctx) { return &ctx->shared; }
+gh::Engine *&gh_ctx_engine(gh_ctx_s *ctx) { return ctx->engine; }
+std::mutex &gh_ctx_engine_mutex(gh_ctx_s *ctx) { return ctx->engine_mu; }
+int gh_ctx_serve_workers(gh_ctx_s *ctx) { return ctx->serve_workers; }
+int gh_ctx_serve_max_batch(gh_ctx_s *ctx) { return ctx->serve_max_batch; }
+gh::MeshH *gh_mesh_host(gh_mesh_s *m) { return &m->h; }
+gh_ctx_s *gh_mesh_ctx(gh_mesh_s *m) { return m->ctx; }
+
 extern "C" {
+
+gh_status gh_serve_config(gh_ctx ctx, int32_t workers, int32_t max_batch) {
+    if (!ctx) { set_error("ctx is NULL"); return GH_EINVAL; }
+    if (workers < 1 || workers > 8 || max_batch < 1 || max_batch > 256) {
+        set_error("workers must be 1..8 and max_batch 1..256");
+        return GH_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(ctx->engine_mu);
+    if (ctx->engine) { set_error("serving already started on this context"); return GH_EBUSY; }
+    ctx->serve_workers = workers;
+    ctx->serve_max_batch = max_batch;
+    return GH_OK;
+}
 
 void gh_params_default(gh_params *p) {
     if (!p) return;
@@ -287,7 +337,9 @@ gh_status gh_ctx_create(int device, size_t hbm_budget_bytes, gh_ctx *out) {
     GH_CUDA(cudaSetDevice(device));
     auto *c = new gh_ctx_s();
     c->c.device = device;
-    c->c.budget = hbm_budget_bytes;
+    c->shared.budget = hbm_budget_bytes;
+    c->c.shared = &c->shared;
+    c->c.launches.p = &c->shared.launches;
     cudaError_t e = cudaDeviceGetAttribute(&c->c.num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->c.status_dev, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->c.status_dev, 0, sizeof(int));
@@ -307,6 +359,8 @@ gh_status gh_mesh_free(gh_mesh mesh);
 
 gh_status gh_ctx_destroy(gh_ctx ctx) {
     if (!ctx) return GH_EINVAL;
+    if (ctx->engine) engine_stop(ctx->engine);
+    ctx->engine = nullptr;
     std::vector<gh_mesh_s *> ms = ctx->meshes;
     for (gh_mesh_s *m : ms) gh_mesh_free(m);
     cudaFree(ctx->c.status_dev);
@@ -323,13 +377,13 @@ gh_status gh_ctx_set_stream(gh_ctx ctx, void *stream) {
 
 gh_status gh_ctx_memory(gh_ctx ctx, size_t *bytes) {
     if (!ctx || !bytes) { set_error("NULL argument"); return GH_EINVAL; }
-    *bytes = ctx->c.in_use;
+    *bytes = ctx->shared.in_use.load();
     return GH_OK;
 }
 
 gh_status gh_ctx_stats(gh_ctx ctx, uint64_t *kernel_launches) {
     if (!ctx || !kernel_launches) { set_error("NULL argument"); return GH_EINVAL; }
-    *kernel_launches = ctx->c.launches;
+    *kernel_launches = ctx->shared.launches.load();
     return GH_OK;
 }
 
@@ -369,6 +423,7 @@ gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, doub
 
 gh_status gh_mesh_free(gh_mesh mesh) {
     if (!mesh) return GH_EINVAL;
+    if (mesh->h.inflight.load() > 0) { set_error("mesh has serving requests in flight"); return GH_EBUSY; }
     gh_ctx_s *ctx = mesh->ctx;
     Ctx *c = &ctx->c;
     cudaStreamSynchronize(c->stream);

@@ -34,6 +34,7 @@
 // is exact, so this is the same arithmetic with an unbounded exponent.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cstddef>
 
 #include "internal.cuh"
@@ -480,7 +481,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     GH_CUDA(cudaFuncSetAttribute(k_gs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs<T>, kThreads, smem));
     if (per_sm < 1) { set_error("diffusion kernel does not fit on an SM"); return GH_EDEVICE; }
-    const int grid = per_sm * c->num_sms;
+    const int grid = std::max(1, per_sm * c->num_sms / std::max(1, c->gs_share));
     if (K > grid) { set_error("internal: more queries than resident CTAs in one diffusion launch"); return GH_EINVAL; }
     std::vector<GsJob<T>> jobs(K);
     size_t soff_total = 0;

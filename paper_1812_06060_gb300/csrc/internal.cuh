@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -82,15 +83,33 @@ struct GridBarrier {
     int pad;
 };
 
+// Accounting shared by a context and its serving workers.
+struct Shared {
+    size_t budget = 0;                              // 0: unlimited
+    std::atomic<size_t> in_use{0};                  // device bytes held
+    std::atomic<unsigned long long> launches{0};    // kernels launched
+};
+
+struct LaunchCounter {
+    std::atomic<unsigned long long> *p = nullptr;
+    LaunchCounter &operator++() {
+        p->fetch_add(1, std::memory_order_relaxed);
+        return *this;
+    }
+};
+
+// What a launcher needs: the device, a stream, a status word and abort flag
+// of its own, and the shared accounting.  The context has one; every serving
+// worker has another with its own stream.
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
-    size_t budget = 0;     // 0: unlimited
-    size_t in_use = 0;
     int num_sms = 0;
+    int gs_share = 1;                // a diffusion launch takes 1/gs_share of the resident CTAs
     int *status_dev = nullptr;       // device status word written by kernels
-    GridBarrier *bar_dev = nullptr;  // grid barrier of the persistent kernels
-    unsigned long long launches = 0; // kernels launched by this context so far
+    GridBarrier *bar_dev = nullptr;  // abort flag of the persistent kernels
+    Shared *shared = nullptr;
+    LaunchCounter launches;
 };
 
 // Resident per-mesh operators (built once by gh_mesh_load).
@@ -152,7 +171,19 @@ struct MeshH {
     int last_k = 0;
     double stage_ms[5] = {0, 0, 0, 0, 0};
     double gs_kernel_ms = 0.0;   // the diffusion kernel alone, last solve
+    std::atomic<int> inflight{0};  // serving requests not yet finished
 };
+
+// The whole path for a list of source sets on one mesh, with the launcher
+// context `c` and the workspace pool `pool` (grown as needed).  d_out_dev:
+// device, [K][nv] (may be null).  stage_ms6 (may be null) gets the stage times.
+gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
+                     const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k);
+size_t ws_bytes(const DevMesh &m, int fp64, int form);
+void free_ws(Ctx *c, QueryWs *w);
+gh_status validate_params(const gh_params *p);
+gh_status prep_sources(const int32_t *src, int32_t nsrc, int64_t nv, std::vector<int32_t> &out);
+bool is_device_ptr(const void *p);
 
 // ---------------------------------------------------------------- kernels (host launchers)
 
