@@ -160,6 +160,98 @@ def oracle_sample(md, src, sweeps_full: int, sample_sweeps: int):
     return sum(per_solve) / len(per_solve), spent
 
 
+def sweeps_for(mesh) -> int:
+    """Sweep count of a serving mesh: about twice its breadth-first depth, the
+    count at which breadth-first Gauss-Seidel has converged (grid side N:
+    depth <= N; icosphere level n: depth <= 3 * 2^n)."""
+    if "N" in mesh.meta:
+        return 2 * int(mesh.meta["N"])
+    return 6 * (1 << int(mesh.meta["level"]))
+
+
+def serve_stream(g, ctx, meshes, handles, n_req, rate, seed, form="edge"):
+    """Poisson arrivals at `rate` requests/s, each on a uniform mesh with 1..16
+    uniform sources; latency = submit to result on the host.  Returns
+    (latencies in ms, wall seconds)."""
+    import numpy as np
+    import meshgen
+    rng = meshgen.rng_for(seed)
+    plan = []
+    t = 0.0
+    for _ in range(n_req):
+        t += -np.log(1.0 - rng.random()) / rate
+        k = int(rng.random() * len(meshes))
+        plan.append((t, k, meshgen.random_sources(rng, meshes[k].nv, 1, 16)))
+    prms = [g.params(gs_sweeps=sweeps_for(m), form=form) for m in meshes]
+    sub_t = [0.0] * n_req
+    done_t = [0.0] * n_req
+    ids = [None] * n_req
+    finished = [False] * n_req
+    stop = threading.Event()
+
+    def collector():
+        outs = {}
+        while not stop.is_set() or not all(finished):
+            progressed = False
+            for i in range(n_req):
+                if ids[i] is None or finished[i]:
+                    continue
+                if ctx.poll(ids[i]):
+                    k = plan[i][1]
+                    out = outs.setdefault(k, np.empty(meshes[k].nv))
+                    ctx.wait(ids[i], out)
+                    done_t[i] = time.perf_counter()
+                    finished[i] = True
+                    progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for i, (ta, k, src) in enumerate(plan):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        sub_t[i] = time.perf_counter()
+        ids[i] = ctx.submit(handles[k], src, prms[k])
+    stop.set()
+    th.join()
+    wall = max(done_t) - t0
+    lat = [1000.0 * (d - s) for s, d in zip(sub_t, done_t)]
+    return lat, wall
+
+
+def serve_summary(g, device, meshes, n_req, rate_factor, seed):
+    """Single-stream capacity of the meshes, then a Poisson stream at
+    rate_factor times that capacity through the serving API."""
+    import numpy as np
+    cap_ctx = g.Context(device)
+    times = []
+    for m in meshes:
+        M = g.Mesh(cap_ctx, m.V, m.F)
+        out = np.empty(m.nv)
+        prm = g.params(gs_sweeps=sweeps_for(m), form="edge")
+        M.solve([0], out, prm)
+        t0 = time.perf_counter()
+        M.solve([1], out, prm)
+        times.append(time.perf_counter() - t0)
+        M.close()
+    cap_ctx.close()
+    capacity = 1.0 / float(np.mean(times))
+    ctx = g.Context(device)
+    handles = [g.Mesh(ctx, m.V, m.F) for m in meshes]
+    lat, wall = serve_stream(g, ctx, meshes, handles, n_req, rate_factor * capacity, seed)
+    for h in handles:
+        h.close()
+    ctx.close()
+    return {"meshes": [f"{m.name} ({m.nv} V)" for m in meshes], "requests": n_req,
+            "single_stream_capacity_solves_per_s": capacity, "offered_rate_per_s": rate_factor * capacity,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "served_solves_per_s": n_req / wall, "form": "edge",
+            "sweeps": "2x breadth-first depth bound per mesh"}
+
+
 def run_reference(args):
     rank, world, _ = _rank()
     if rank != 0:
@@ -272,6 +364,36 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_value = world * len(FORMS) * args.steps / e2e_s
 
+    # K right-hand sides of the same grid in one batch against the single-query rate
+    batch = None
+    if world == 1 and not args.no_extras:
+        K = 8
+        rng = meshgen.rng_for(meshgen.config_seed(2) + 99)
+        sets = [meshgen.random_sources(rng, mesh.nv, 1, 1) for _ in range(K)]
+        bout = torch.empty((K, mesh.nv), dtype=torch.float64, device="cuda")
+        M.solve_batch(sets, bout, prm["edge"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        M.solve_batch(sets, bout, prm["edge"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1)
+        e0.record(stream)
+        for sset in sets[:2]:
+            M.solve(sset, out["edge"], prm["edge"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sms = e0.elapsed_time(e1) / 2
+        batch = {"K": K, "form": "edge", "batched_solves_per_s": K / (bms / 1000.0),
+                 "single_solves_per_s": 1.0 / (sms / 1000.0), "speedup": (K / bms) / (1.0 / sms)}
+    serve = None
+    if world == 1 and not args.no_extras:
+        sm = [meshgen.jittered_grid(257, meshgen.config_seed(4, 1)), meshgen.jittered_grid(513, meshgen.config_seed(4, 2)),
+              meshgen.noisy_icosphere(6, meshgen.config_seed(4, 6)), meshgen.noisy_icosphere(7, meshgen.config_seed(4, 7))]
+        serve = serve_summary(g, local, sm, 120, 1.0, meshgen.config_seed(4, 100))
+
     peak, peak_kind = measured_peaks()
     bytes_launch = gs_bytes(mesh.nv, M.ne, SWEEPS)
     gs_avg_ms = statistics.mean(gs_ms)
@@ -297,6 +419,8 @@ def run_ours(args):
             "stage_ms_last_solve": dict(zip(["bfs_layout", "diffusion", "normalize", "admm", "integrate",
                                              "k_gs"], [round(x, 4) for x in M.stage_times()])),
             "clocks": clk.summary(),
+            "batch": batch,
+            "serve": serve,
         }
         if world == 1 and not args.no_cpu_baseline:
             import oracle
@@ -316,6 +440,107 @@ def run_ours(args):
     return 0
 
 
+def run_workload(args):
+    """The other configurations, one JSON line each (not the default bench):
+    c3  noisy icosphere level 10 (10.5M V), 64 source sets of 1..8 vertices as
+        K = 64 right-hand sides, edge form 700 sweeps (face form 1200 with
+        --form face); batched solves/s against the single-query rate
+    c4  serving stream over 10 meshes (grids 101..2000, noisy icospheres 5..9)
+        at rates 0.25..4 x single-stream capacity: p50/p99 latency, solves/s
+    c5  sinusoid icosphere level 12 (168M V), edge form, m = 10, 4000 sweeps,
+        one source: solve time and device memory"""
+    import numpy as np
+    import torch
+    import meshgen
+    from paper_1812_06060_gb300 import build as gbuild
+    gbuild.build()
+    import paper_1812_06060_gb300 as g
+    g.load_library()
+    dev = 0
+    torch.cuda.set_device(dev)
+    out = {"workload": args.workload, "data": "synthetic", "dtype": "f32"}
+    if args.workload == "c3":
+        t0 = time.perf_counter()
+        w = meshgen.workload_c3()
+        out["generate_s"] = time.perf_counter() - t0
+        form = args.form
+        sweeps = w.gs_face if form == "face" else w.gs_edge
+        ctx = g.Context(dev)
+        t0 = time.perf_counter()
+        M = g.Mesh(ctx, w.mesh.V, w.mesh.F)
+        torch.cuda.synchronize()
+        out["mesh_load_s"] = time.perf_counter() - t0
+        prm = g.params(gs_sweeps=sweeps, form=form, m=w.m)
+        one = torch.empty(w.mesh.nv, dtype=torch.float64, device="cuda")
+        M.solve(w.sources[0], one, prm)
+        t0 = time.perf_counter()
+        M.solve(w.sources[1], one, prm)
+        single_s = time.perf_counter() - t0
+        st1 = M.stage_times()
+        K = len(w.sources)
+        dout = torch.empty((K, w.mesh.nv), dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        M.solve_batch(w.sources, dout, prm)
+        batch_s = time.perf_counter() - t0
+        stb = M.stage_times()
+        V = w.mesh.nv
+        out.update({"config": f"noisy icosphere level 10 ({V} V, {w.mesh.nf} F), K={K} source sets of 1..8 vertices, "
+                              f"{form} form, {sweeps} sweeps, 10 ADMM iterations",
+                    "single_solves_per_s": 1.0 / single_s, "batched_solves_per_s": K / batch_s,
+                    "speedup": (K / batch_s) * single_s, "single_stage_ms": list(st1), "batch_stage_ms": list(stb),
+                    "gs_vertex_updates_per_s_batch": K * sweeps * V / (stb[5] / 1000.0),
+                    "gs_algorithmic_GBps_batch": K * gs_bytes(V, M.ne, sweeps) / (stb[5] / 1000.0) / 1e9,
+                    "device_bytes": ctx.memory()})
+        d = dout.cpu().numpy()
+        out["finite_fraction"] = float(np.isfinite(d).mean())
+        M.close()
+        ctx.close()
+    elif args.workload == "c4":
+        meshes = meshgen.serving_meshes()
+        res = []
+        for rf in (0.25, 0.5, 1.0, 2.0, 4.0):
+            r = serve_summary(g, dev, meshes, args.requests, rf, meshgen.config_seed(4, 200) + int(rf * 100))
+            res.append({"rate_factor": rf, **{k: r[k] for k in ("offered_rate_per_s", "p50_ms", "p99_ms",
+                                                              "served_solves_per_s",
+                                                              "single_stream_capacity_solves_per_s")}})
+        out.update({"config": "10 meshes: jittered grids 101, 257, 513, 1025, 2000 and noisy icospheres 5..9; "
+                              "1..16 uniform sources; edge form; sweeps 2x breadth-first depth bound",
+                    "requests_per_rate": args.requests, "rates": res})
+    elif args.workload == "c5":
+        t0 = time.perf_counter()
+        w = meshgen.workload_c5()
+        out["generate_s"] = time.perf_counter() - t0
+        V = w.mesh.nv
+        ctx = g.Context(dev)
+        t0 = time.perf_counter()
+        M = g.Mesh(ctx, w.mesh.V, w.mesh.F)
+        torch.cuda.synchronize()
+        out["mesh_load_s"] = time.perf_counter() - t0
+        out["mesh_device_bytes"] = ctx.memory()
+        prm = g.params(gs_sweeps=w.gs_edge, form="edge", m=w.m)
+        d = torch.empty(V, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        M.solve(w.sources[0], d, prm)
+        torch.cuda.synchronize()
+        solve_s = time.perf_counter() - t0
+        st = M.stage_times()
+        dh = d.cpu().numpy()
+        P = w.mesh.V
+        chord = np.linalg.norm(P - P[w.sources[0][0]], axis=1)
+        out.update({"config": f"sinusoid icosphere level 12 ({V} V, {w.mesh.nf} F), edge form, m = {w.m}, "
+                              f"{w.gs_edge} sweeps, one source", "solve_s": solve_s, "stage_ms": list(st),
+                    "gs_vertex_updates_per_s": w.gs_edge * V / (st[5] / 1000.0),
+                    "gs_algorithmic_GBps": gs_bytes(V, M.ne, w.gs_edge) / (st[5] / 1000.0) / 1e9,
+                    "device_bytes_peak_held": ctx.memory(),
+                    "finite_fraction": float(np.isfinite(dh).mean()),
+                    "min_d_over_chord": float(np.min(dh[chord > 0] / chord[chord > 0])),
+                    "max_d": float(np.max(dh))})
+        M.close()
+        ctx.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     global SWEEPS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -324,6 +549,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: the benchmark line; c3/c4/c5: the batched, serving and giant-mesh configurations")
+    ap.add_argument("--form", default="edge", choices=["face", "edge"])
+    ap.add_argument("--requests", type=int, default=400, help="requests per rate (c4)")
     ap.add_argument("--sweeps", type=int, default=SWEEPS,
                     help="Gauss-Seidel sweeps per solve (a smaller case for profiling; the benchmark is 2000)")
     args = ap.parse_args()
@@ -332,6 +562,8 @@ def main():
         SWEEPS = args.sweeps
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        return run_workload(args)
     return run_ours(args)
 
 

@@ -177,32 +177,30 @@ def icosphere(level: int) -> Mesh:
 def vertex_adjacency(nv: int, F: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """CSR one-ring of each vertex (neighbours in ascending order); used only
     to smooth the synthetic noise field."""
+    import scipy.sparse as sp
     F = F.astype(np.int64)
     a = np.concatenate([F[:, 0], F[:, 1], F[:, 2], F[:, 1], F[:, 2], F[:, 0]])
     b = np.concatenate([F[:, 1], F[:, 2], F[:, 0], F[:, 0], F[:, 1], F[:, 2]])
-    key = np.unique(a * nv + b)
-    src = key // nv
-    dst = key % nv
-    rowptr = np.zeros(nv + 1, dtype=np.int64)
-    np.add.at(rowptr, src + 1, 1)
-    rowptr = np.cumsum(rowptr)
-    return rowptr, dst
+    A = sp.csr_matrix((np.ones(a.size, np.int8), (a, b)), shape=(nv, nv))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A.indptr.astype(np.int64), A.indices.astype(np.int64)
 
 
 def noisy_icosphere(level: int, seed: int, amplitude: float = 0.02, smooth_rounds: int = 3) -> Mesh:
     """Icosphere with radial noise r = 1 + amplitude * n, where n is a
     per-vertex standard normal field averaged ``smooth_rounds`` times over
     each vertex's closed one-ring (the vertex and its neighbours)."""
+    import scipy.sparse as sp
     m = icosphere(level)
     rng = rng_for(seed)
     n = normal(rng, m.nv)
     rowptr, col = vertex_adjacency(m.nv, m.F)
     deg = np.diff(rowptr)
-    row = np.repeat(np.arange(m.nv), deg)
+    # closed one-ring sum as a sparse matrix (adjacency + identity)
+    A = sp.csr_matrix((np.ones(col.size), col, rowptr), shape=(m.nv, m.nv)) + sp.identity(m.nv, format="csr")
     for _ in range(smooth_rounds):
-        s = np.zeros(m.nv)
-        np.add.at(s, row, n[col])
-        n = (s + n) / (deg + 1.0)
+        n = (A @ n) / (deg + 1.0)
     r = 1.0 + amplitude * n
     m.V = m.V * r[:, None]
     m.name = f"noisy_icosphere{level}"
