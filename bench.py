@@ -48,6 +48,31 @@ def _rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_sources(rank: int, nv: int, base_sources):
+    """Replicas only: rank 0 solves the workload's source, every other rank a
+    seeded source of its own (the queries are independent; nothing is
+    exchanged between ranks on the data path)."""
+    import meshgen
+    if rank == 0:
+        return base_sources
+    return meshgen.random_sources(meshgen.rng_for(meshgen.config_seed(2) + 7 * rank), nv, 1, 1)
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """The slowest rank's time (the job ends when the last replica ends)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, solves_per_step: int, steps: int, total_ms: float) -> float:
+    """Solves of all ranks per second of the slowest rank (weak scaling)."""
+    return world * solves_per_step * steps / (total_ms / 1000.0)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -305,8 +330,7 @@ def run_ours(args):
 
     w = meshgen.workload_c2(GRID_N)
     mesh = w.mesh
-    src_np = w.sources[0] if rank == 0 else meshgen.random_sources(meshgen.rng_for(meshgen.config_seed(2) + 7 * rank),
-                                                                   mesh.nv, 1, 1)
+    src_np = rank_sources(rank, mesh.nv, w.sources[0])
     stream = torch.cuda.current_stream()
     ctx = g.Context(local, stream=stream)
     M = g.Mesh(ctx, torch.from_numpy(mesh.V).cuda(), torch.from_numpy(mesh.F).cuda())
@@ -337,13 +361,9 @@ def run_ours(args):
             evs[i][1].record(stream)
         torch.cuda.synchronize()
     launches = ctx.kernel_launches() - l0
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * len(FORMS) * args.steps / (total_ms / 1000.0)
+    value = whole_job_value(world, len(FORMS), args.steps, total_ms)
 
     # end to end through the public API with host buffers: the source set is
     # copied from pinned host memory, the distances back into pinned memory
@@ -358,11 +378,8 @@ def run_ours(args):
         for f in FORMS:
             M.solve(src_host, out_host[f], prm[f])
         e2e_s += time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * len(FORMS) * args.steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_value = whole_job_value(world, len(FORMS), args.steps, 1000.0 * e2e_s)
 
     # K right-hand sides of the same grid in one batch against the single-query rate
     batch = None

@@ -103,6 +103,13 @@ gh_status gh_ctx_destroy(gh_ctx ctx);
  * alive while the context uses it. */
 gh_status gh_ctx_set_stream(gh_ctx ctx, void *stream);
 
+/* Limit of every dependency wait inside the persistent diffusion kernel
+ * (microseconds; <= 0 restores the default of 2 s).  When a wait runs out,
+ * the kernel raises its abort flag, every CTA leaves after its staged copies
+ * have landed, and the solve returns GH_ETIMEOUT; the context stays usable.
+ * Applies to the context's blocking solves. */
+gh_status gh_ctx_set_wait_limit(gh_ctx ctx, int64_t microseconds);
+
 /* Device bytes the context holds now. */
 gh_status gh_ctx_memory(gh_ctx ctx, size_t *bytes_in_use);
 

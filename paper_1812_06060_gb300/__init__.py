@@ -32,7 +32,8 @@ STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: 
                 6: "GH_ENOTFOUND", 7: "GH_ENONMANIFOLD"}
 
 # symbols declared in include/geoheat.h
-EXPORTS = ["gh_params_default", "gh_version", "gh_ctx_create", "gh_ctx_destroy", "gh_ctx_set_stream", "gh_ctx_memory", "gh_ctx_stats",
+EXPORTS = ["gh_params_default", "gh_version", "gh_ctx_create", "gh_ctx_destroy", "gh_ctx_set_stream", "gh_ctx_set_wait_limit", "gh_ctx_memory",
+           "gh_ctx_stats",
            "gh_mesh_load", "gh_mesh_info", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
            "gh_debug_dump", "gh_stage_times", "gh_mean_edge_length_noalloc", "gh_serve_config", "gh_submit", "gh_poll",
            "gh_wait", "gh_last_error"]
@@ -73,6 +74,8 @@ def load_library(path: str = LIB_PATH):
     L.gh_ctx_destroy.argtypes = [P]
     L.gh_ctx_set_stream.restype = S
     L.gh_ctx_set_stream.argtypes = [P, P]
+    L.gh_ctx_set_wait_limit.restype = S
+    L.gh_ctx_set_wait_limit.argtypes = [P, I64]
     L.gh_ctx_memory.restype = S
     L.gh_ctx_memory.argtypes = [P, C.POINTER(C.c_size_t)]
     L.gh_ctx_stats.restype = S
@@ -148,6 +151,10 @@ class Context:
         """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None."""
         raw = getattr(stream, "cuda_stream", stream)
         _check(lib().gh_ctx_set_stream(self.handle, C.c_void_p(raw or 0)))
+
+    def set_wait_limit(self, microseconds: int):
+        """Limit of the diffusion kernel's dependency waits (<= 0: 2 s)."""
+        _check(lib().gh_ctx_set_wait_limit(self.handle, microseconds))
 
     def memory(self) -> int:
         n = C.c_size_t()

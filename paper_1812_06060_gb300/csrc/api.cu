@@ -375,6 +375,12 @@ gh_status gh_ctx_set_stream(gh_ctx ctx, void *stream) {
     return GH_OK;
 }
 
+gh_status gh_ctx_set_wait_limit(gh_ctx ctx, int64_t microseconds) {
+    if (!ctx) { set_error("ctx is NULL"); return GH_EINVAL; }
+    ctx->c.wait_limit_ns = microseconds > 0 ? (unsigned long long)microseconds * 1000ull : 2000000000ull;
+    return GH_OK;
+}
+
 gh_status gh_ctx_memory(gh_ctx ctx, size_t *bytes) {
     if (!ctx || !bytes) { set_error("NULL argument"); return GH_EINVAL; }
     *bytes = ctx->shared.in_use.load();

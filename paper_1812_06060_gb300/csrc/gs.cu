@@ -43,7 +43,7 @@ namespace gh {
 
 namespace {
 
-constexpr unsigned long long kWaitTimeoutNs = 2000000000ull;  // 2 s for any single wait
+constexpr unsigned long long kWaitTimeoutNs = 2000000000ull;  // 2 s for a staging-barrier wait
 constexpr int kMaxDeg = 8;                                    // row entries held in registers
 
 template <class T> struct GsJob {
@@ -212,7 +212,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // loads that go out together; once all are met one acquire fence orders the
 // tile's reads after the releases observed.  Bounded like every wait.
 __device__ bool wait_sets(const int32_t *p0, int t0, const int32_t *p1, int t1, const int32_t *p2, int t2,
-                          int *abort_flag, int *status) {
+                          unsigned long long limit_ns, int *abort_flag, int *status) {
     const unsigned long long tstart = gtime();
     for (unsigned n = 0;; ++n) {
         const int v0 = (t0 > 0) ? ld_relaxed(p0) : 0;
@@ -224,7 +224,7 @@ __device__ bool wait_sets(const int32_t *p0, int t0, const int32_t *p1, int t1, 
         }
         if ((n & 31) == 31) {
             if (*(volatile int *)abort_flag) return false;
-            if (gtime() - tstart > kWaitTimeoutNs) {
+            if (gtime() - tstart > limit_ns) {
                 atomicExch(abort_flag, 1);
                 atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
                 return false;
@@ -286,7 +286,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // sweep k once its counter reaches (k + 1) * nt.
 template <class T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
-    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nsweeps, int *abort_flag, int *status) {
+    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nsweeps, unsigned long long wait_limit_ns, int *abort_flag,
+         int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage<T> *stage = reinterpret_cast<Stage<T> *>(smem_raw);
     __shared__ __align__(8) uint64_t full[2], empty[2];
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                         const int t1 = (k > 0) ? k * d.nt_self : 0;
                         const int t2 = (k > 0) ? k * d.nt_next : 0;
                         ok = wait_sets(J.done + (i > 0 ? i - 1 : 0), t0, J.done + i, t1, J.done + i + 1, t2,
-                                       abort_flag, status) ? 1 : 0;
+                                       wait_limit_ns, abort_flag, status) ? 1 : 0;
                         S.abort = ok ? 0 : 1;
                         mbar_arrive(&full[b]);
                     }
@@ -535,7 +536,9 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     int njobs = K;
     int *status = c->status_dev;
     int *abort_flag = &c->bar_dev->abort;
-    void *argv[] = {(void *)&djobs, (void *)&njobs, (void *)&sweeps, (void *)&abort_flag, (void *)&status};
+    unsigned long long wait_limit_ns = c->wait_limit_ns;
+    void *argv[] = {(void *)&djobs, (void *)&njobs, (void *)&sweeps, (void *)&wait_limit_ns, (void *)&abort_flag,
+                    (void *)&status};
     if (ev0) cudaEventRecord(ev0, st);
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_gs<T>, dim3(grid), dim3(kThreads), argv, smem, st);
     ++c->launches;

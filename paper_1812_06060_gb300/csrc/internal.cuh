@@ -106,6 +106,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int gs_share = 1;                // a diffusion launch takes 1/gs_share of the resident CTAs
+    unsigned long long wait_limit_ns = 2000000000ull;  // limit of any dependency wait inside a kernel
     int *status_dev = nullptr;       // device status word written by kernels
     GridBarrier *bar_dev = nullptr;  // abort flag of the persistent kernels
     Shared *shared = nullptr;

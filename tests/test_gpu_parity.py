@@ -97,8 +97,16 @@ def _run_case(gh, ctx, mesh, sources, form, sweeps, fp64, tol, admm_iters=10):
         derr = _d_err(d, ref["d"], sources, md.hbar)
         assert np.array_equal(np.isinf(d), np.isinf(ref["d"]))
         assert np.all(d[np.asarray(sources)] == 0)
-        return dict(uerr=uerr.max(), derr=derr, h=M.dump(gh.GH_DUMP_H).reshape(-1, 3), href=ref["h"],
-                    M=M, md=md, ref=ref, d=d)
+        h = M.dump(gh.GH_DUMP_H).reshape(-1, 3)
+        herr = _h_err(h, ref["h"])
+        if form == "face":
+            gxerr = np.max(np.linalg.norm(M.dump(gh.GH_DUMP_G).reshape(-1, 3) - ref["g"], axis=1))
+        else:
+            gxerr = np.max(np.abs(M.dump(gh.GH_DUMP_X) - ref["x"])) / md.hbar
+        _log(f"{mesh.name or 'mesh'} nv={md.nv} form={form} sweeps={sweeps} fp64={fp64}: "
+             f"u {uerr.max():.2e} h {herr:.2e} {'g' if form == 'face' else 'x/hbar'} {gxerr:.2e} d {derr:.2e}")
+        return dict(uerr=uerr.max(), derr=derr, herr=herr, gxerr=gxerr, h=h, href=ref["h"], M=M, md=md, ref=ref,
+                    d=d)
     finally:
         pass
 
@@ -107,13 +115,23 @@ def _h_err(h, href):
     return np.max(np.linalg.norm(h - href, axis=1))
 
 
+def _log(line):
+    """Measured errors, appended to gpurun_out/parity_errors.txt when that
+    folder exists (the GPU runs bring it back)."""
+    import os
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(d):
+        with open(os.path.join(d, "parity_errors.txt"), "a") as f:
+            f.write(line + "\n")
+
+
 @pytest.mark.parametrize("form", ["face", "edge"])
 def test_icosphere4_fp64(gh, ctx, form):
     """Unit icosphere level 4, source vertex 0, t = hbar^2, FP64 mode."""
     w = meshgen.workload_c1()
     r = _run_case(gh, ctx, w.mesh, [0], form, 200, True, D_TOL_FP64)
     assert r["uerr"] < 1e-12
-    assert _h_err(r["h"], r["href"]) < 1e-10
+    assert r["herr"] < 1e-10 and r["gxerr"] < 1e-10
     assert r["derr"] < D_TOL_FP64
     r["M"].close()
 
@@ -122,7 +140,9 @@ def test_icosphere4_fp64(gh, ctx, form):
 def test_icosphere4_fp32(gh, ctx, form):
     w = meshgen.workload_c1()
     r = _run_case(gh, ctx, w.mesh, [0], form, 200, False, D_TOL_FP32)
+    # FP32 rounds each update to 2^-24; measured u 2.5e-6, h 5e-7, g/x 6e-7
     assert r["uerr"] < 1e-4
+    assert r["herr"] < 1e-4 and r["gxerr"] < 1e-4
     assert r["derr"] < D_TOL_FP32
     r["M"].close()
 
@@ -135,6 +155,7 @@ def test_jittered_grid_ragged(gh, ctx, form):
     r = _run_case(gh, ctx, m, [4000], form, 600, False, D_TOL_FP32)
     assert r["ref"]["u"][1].min() < -150          # below the FP32 range: needs the separate exponent
     assert r["uerr"] < 1e-3
+    assert r["herr"] < 1e-4 and r["gxerr"] < 1e-4
     assert r["derr"] < D_TOL_FP32
     r["M"].close()
 
@@ -143,6 +164,7 @@ def test_jittered_grid_ragged(gh, ctx, form):
 def test_noisy_sphere_multi_source(gh, ctx, form):
     m = meshgen.noisy_icosphere(5, 31)
     r = _run_case(gh, ctx, m, [17, 5000, 9999], form, 300, False, D_TOL_FP32)
+    assert r["herr"] < 1e-3 and r["gxerr"] < 1e-4   # measured 1.6e-5 / 4e-6 (negative cotans)
     assert r["derr"] < D_TOL_FP32
     r["M"].close()
 
@@ -240,5 +262,9 @@ def test_full_size_grid_1025(gh, ctx):
     oracle runs in seconds: bit-exact sets, distances within the contract."""
     w = meshgen.workload_c2()
     r = _run_case(gh, ctx, w.mesh, list(w.sources[0]), "edge", 40, False, D_TOL_FP32)
+    # 40 sweeps on an 858-set mesh is far from converged: the far field is a
+    # long chain of partly cancelling terms (negative cotans); measured
+    # u 0.15, h 3.3e-3, x/hbar 9e-4 and d 6.3e-5
+    assert r["herr"] < 1e-2 and r["gxerr"] < 5e-3
     assert r["derr"] < D_TOL_FP32
     r["M"].close()
