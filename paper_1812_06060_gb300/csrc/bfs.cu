@@ -10,6 +10,8 @@
 // a parent then counts the neighbours whose key is its own, an exclusive scan
 // over the parents in rank order gives each parent's first child position.
 // One CTA walks all sets of one query (one CTA per query of a batch).
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 namespace gh {
@@ -57,80 +59,137 @@ __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
     return total;
 }
 
-constexpr int kBfsChunks = 4;   // parents per thread whose rows stay in registers between the passes
+constexpr int kBfsChunks = 4;   // parent chunks per thread whose rows stay in registers between the passes
+constexpr int kBfsCluster = 8;  // CTAs (one cluster) walking the sets of one query
 
 // Keys: a vertex discovered by the parent of rank r through the parent's
 // slot j holds (r << 32 | j); sources hold 0; undiscovered vertices hold the
 // maximum.  A discovered vertex always holds a key below every key a later
 // set offers, so the offers need no "already visited" test.
+//
+// One cluster of kBfsCluster CTAs walks the sets of one query.  The parents
+// of a set (a contiguous range of queue ranks) are split into kBfsCluster
+// contiguous parts, one per CTA.  Per set: every CTA offers its parents' keys
+// (64-bit atomicMin), cluster barrier; every CTA counts its parents' children
+// and scans them, publishes its total in shared memory, cluster barrier;
+// each CTA reads the totals of the lower-ranked CTAs through distributed
+// shared memory to place its children, writes them, cluster barrier.
+__device__ __forceinline__ unsigned long long bfs_key(int r, int slot) {
+    return ((unsigned long long)(unsigned)r << 32) | (unsigned)slot;
+}
+
 __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
-    const BfsArgs a = all[blockIdx.x];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const BfsArgs a = all[blockIdx.x / kBfsCluster];
+    __shared__ int s_total;
     int lo = 0, hi = a.n0, nlev = 1;
-    if (threadIdx.x == 0) a.lvl_off[0] = 0;
+    if (crank == 0 && threadIdx.x == 0) a.lvl_off[0] = 0;
     while (true) {
         const int n = hi - lo;
-        const int nchunk = (n + BT - 1) / BT;
+        const int per = (n + kBfsCluster - 1) / kBfsCluster;
+        const int mlo = min(hi, lo + crank * per), mhi = min(hi, mlo + per);
+        const int nchunk = (mhi - mlo + BT - 1) / BT;
         int pp[kBfsChunks], rb[kBfsChunks], re[kBfsChunks];
-        // every parent offers its key to all its neighbours
+        // offers
 #pragma unroll
         for (int c = 0; c < kBfsChunks; ++c) {
-            const int r = lo + c * BT + (int)threadIdx.x;
+            const int r = mlo + c * BT + (int)threadIdx.x;
             int p = -1, b = 0, e = 0;
-            if (c < nchunk && r < hi) {
+            if (c < nchunk && r < mhi) {
                 p = __ldcg(&a.order[r]);
                 b = a.rowptr[p];
                 e = a.rowptr[p + 1];
-                for (int j = b; j < e; ++j)
-                    atomicMin(&a.key[a.col[j]], ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b));
+                for (int j = b; j < e; ++j) atomicMin(&a.key[a.col[j]], bfs_key(r, j - b));
             }
             pp[c] = p; rb[c] = b; re[c] = e;
         }
         for (int c = kBfsChunks; c < nchunk; ++c) {
-            const int r = lo + c * BT + (int)threadIdx.x;
-            if (r < hi) {
+            const int r = mlo + c * BT + (int)threadIdx.x;
+            if (r < mhi) {
                 const int p = __ldcg(&a.order[r]);
                 const int b = a.rowptr[p], e = a.rowptr[p + 1];
-                for (int j = b; j < e; ++j)
-                    atomicMin(&a.key[a.col[j]], ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b));
+                for (int j = b; j < e; ++j) atomicMin(&a.key[a.col[j]], bfs_key(r, j - b));
             }
         }
-        __syncthreads();
-        // children in (parent rank, slot) order
-        int base = hi;
+        cluster.sync();
+        // children per parent, scanned over this CTA's parents in rank order
+        int cnt[kBfsChunks], ex[kBfsChunks], ctot[kBfsChunks];
+        unsigned mask[kBfsChunks];
+        int mytotal = 0;
         for (int c = 0; c < nchunk; ++c) {
-            const int r = lo + c * BT + (int)threadIdx.x;
+            const int r = mlo + c * BT + (int)threadIdx.x;
             int p = -1, b = 0, e = 0;
             if (c < kBfsChunks) {
 #pragma unroll
                 for (int x = 0; x < kBfsChunks; ++x)
                     if (x == c) { p = pp[x]; b = rb[x]; e = re[x]; }
-            } else if (r < hi) {
+            } else if (r < mhi) {
                 p = __ldcg(&a.order[r]);
                 b = a.rowptr[p];
                 e = a.rowptr[p + 1];
             }
-            int cnt = 0;
-            unsigned mine_mask = 0;   // slots (up to 32) whose neighbour this parent discovered
-            if (r < hi) {
+            int k = 0;
+            unsigned mk = 0;
+            if (r < mhi) {
                 for (int j = b; j < e; ++j) {
-                    const unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
-                    if (__ldcg(&a.key[a.col[j]]) == mine) {
-                        ++cnt;
-                        if (j - b < 32) mine_mask |= 1u << (j - b);
+                    if (__ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b)) {
+                        ++k;
+                        if (j - b < 32) mk |= 1u << (j - b);
                     }
                 }
             }
             int excl;
-            const int total = bt_scan(cnt, excl);
-            if (cnt) {
-                int at = base + excl;
+            const int tot = bt_scan(k, excl);
+            if (c < kBfsChunks) {
+#pragma unroll
+                for (int x = 0; x < kBfsChunks; ++x)
+                    if (x == c) { cnt[x] = k; ex[x] = excl; ctot[x] = tot; mask[x] = mk; }
+            }
+            mytotal += tot;
+        }
+        if (threadIdx.x == 0) s_total = mytotal;
+        cluster.sync();
+        int before = 0, total = 0;
+        for (int q = 0; q < kBfsCluster; ++q) {
+            const int t = *cluster.map_shared_rank(&s_total, q);
+            if (q < crank) before += t;
+            total += t;
+        }
+        // place the children: queue position hi + before + (children of this
+        // CTA's earlier chunks) + (earlier parents of the chunk)
+        int base_run = 0;
+        for (int c = 0; c < nchunk; ++c) {
+            const int r = mlo + c * BT + (int)threadIdx.x;
+            int p = -1, b = 0, e = 0, k = 0, excl = 0, tot = 0;
+            unsigned mk = 0;
+            if (c < kBfsChunks) {
+#pragma unroll
+                for (int x = 0; x < kBfsChunks; ++x)
+                    if (x == c) { p = pp[x]; b = rb[x]; e = re[x]; k = cnt[x]; excl = ex[x]; tot = ctot[x]; mk = mask[x]; }
+            } else {
+                // chunks past kBfsChunks: count again (same keys, same result) and rescan
+                if (r < mhi) {
+                    p = __ldcg(&a.order[r]);
+                    b = a.rowptr[p];
+                    e = a.rowptr[p + 1];
+                    for (int j = b; j < e; ++j)
+                        if (__ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b)) {
+                            ++k;
+                            if (j - b < 32) mk |= 1u << (j - b);
+                        }
+                }
+                tot = bt_scan(k, excl);
+            }
+            if (k) {
+                int at = hi + before + base_run + excl;
                 for (int j = b; j < e; ++j) {
                     bool is_child;
                     if (j - b < 32) {
-                        is_child = (mine_mask >> (j - b)) & 1u;
+                        is_child = (mk >> (j - b)) & 1u;
                     } else {
-                        const unsigned long long mine = ((unsigned long long)(unsigned)r << 32) | (unsigned)(j - b);
-                        is_child = __ldcg(&a.key[a.col[j]]) == mine;
+                        is_child = __ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b);
                     }
                     if (is_child) {
                         const int w = a.col[j];
@@ -140,16 +199,16 @@ __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
                     }
                 }
             }
-            base += total;
+            base_run += tot;
         }
-        __syncthreads();
-        if (base == hi) break;
-        if (threadIdx.x == 0) a.lvl_off[nlev] = hi;
+        cluster.sync();
+        if (total == 0) break;
+        if (crank == 0 && threadIdx.x == 0) a.lvl_off[nlev] = hi;
         ++nlev;
         lo = hi;
-        hi = base;
+        hi += total;
     }
-    if (threadIdx.x == 0) {
+    if (crank == 0 && threadIdx.x == 0) {
         a.lvl_off[nlev] = hi;
         a.meta[0] = nlev;
         a.meta[1] = hi;
@@ -272,7 +331,26 @@ gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const st
     BfsArgs *dargs = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&dargs, sizeof(BfsArgs) * K, st));
     GH_CUDA(cudaMemcpyAsync(dargs, args.data(), sizeof(BfsArgs) * K, cudaMemcpyHostToDevice, st));
-    k_bfs<<<K, BT, 0, st>>>(dargs); ++c->launches;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(K * kBfsCluster);
+        cfg.blockDim = dim3(BT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kBfsCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t le0 = cudaLaunchKernelEx(&cfg, k_bfs, (const BfsArgs *)dargs);
+        ++c->launches;
+        if (le0 != cudaSuccess) {
+            cudaFreeAsync(dargs, st);
+            return cuda_fail(le0, "cluster launch of k_bfs");
+        }
+    }
     cudaError_t le = cudaGetLastError();
     cudaFreeAsync(dargs, st);
     if (le != cudaSuccess) return cuda_fail(le, "k_bfs");
