@@ -262,6 +262,29 @@ def jittered_grid(N: int, seed: int | None, jitter: float = 0.2) -> Mesh:
     return Mesh(V=V, F=F, name=f"grid{N}", meta={"N": N, "seed": seed, "jitter": jitter})
 
 
+def strip_grid(nx: int, ny: int) -> Mesh:
+    """Regular ny x nx vertex grid with unit spacing (vertex (i, j) = index
+    i*nx + j at (x, y) = (j, i)), cells split by the same alternating
+    diagonals as ``jittered_grid``.  With the first row as sources every
+    breadth-first set is a row of about nx vertices: a long, shallow
+    front for exercising wide sets."""
+    i, j = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    V = np.zeros((nx * ny, 3))
+    V[:, 0] = j.ravel().astype(np.float64)
+    V[:, 1] = i.ravel().astype(np.float64)
+    ci, cj = np.meshgrid(np.arange(ny - 1), np.arange(nx - 1), indexing="ij")
+    ci, cj = ci.ravel(), cj.ravel()
+    v00 = ci * nx + cj
+    v01 = v00 + 1
+    v10 = v00 + nx
+    v11 = v10 + 1
+    even = (ci + cj) % 2 == 0
+    t1 = np.where(even[:, None], np.stack([v00, v01, v11], 1), np.stack([v00, v01, v10], 1))
+    t2 = np.where(even[:, None], np.stack([v00, v11, v10], 1), np.stack([v01, v11, v10], 1))
+    F = np.stack([t1, t2], axis=1).reshape(-1, 3).astype(np.int32)
+    return Mesh(V=V, F=F, name=f"strip{nx}x{ny}", meta={"nx": nx, "ny": ny})
+
+
 # --------------------------------------------------------------------------
 # Source sets
 # --------------------------------------------------------------------------

@@ -87,6 +87,7 @@ gh_status check_status(Ctx *c, const char *stage) {
     case DEV_EINVAL: set_error(std::string(stage) + ": invalid input (index out of range or repeated vertex in a face)"); return GH_EINVAL;
     case DEV_ENONMANIFOLD: set_error(std::string(stage) + ": mesh is not an oriented 2-manifold"); return GH_ENONMANIFOLD;
     case DEV_ETIMEOUT: set_error(std::string(stage) + ": a grid barrier wait ran out"); return GH_ETIMEOUT;
+    case DEV_EINTERNAL: set_error(std::string(stage) + ": internal consistency check failed (breadth-first layout)"); return GH_EDEVICE;
     default: set_error(std::string(stage) + ": device error"); return GH_EDEVICE;
     }
 }

@@ -59,23 +59,45 @@ __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
     return total;
 }
 
-constexpr int kBfsChunks = 4;   // parent chunks per thread whose rows stay in registers between the passes
 constexpr int kBfsCluster = 8;  // CTAs (one cluster) walking the sets of one query
 
-// Keys: a vertex discovered by the parent of rank r through the parent's
-// slot j holds (r << 32 | j); sources hold 0; undiscovered vertices hold the
-// maximum.  A discovered vertex always holds a key below every key a later
-// set offers, so the offers need no "already visited" test.
+// Keys: a vertex discovered by the parent of queue rank r through the
+// parent's slot j holds ((r + 1) << 32 | j); sources hold 0 and undiscovered
+// vertices the maximum, so no offer can equal a source's key.  A discovered
+// vertex always holds a key below every key a later set offers, so the
+// offers need no "already visited" test.
 //
 // One cluster of kBfsCluster CTAs walks the sets of one query.  The parents
 // of a set (a contiguous range of queue ranks) are split into kBfsCluster
-// contiguous parts, one per CTA.  Per set: every CTA offers its parents' keys
-// (64-bit atomicMin), cluster barrier; every CTA counts its parents' children
-// and scans them, publishes its total in shared memory, cluster barrier;
-// each CTA reads the totals of the lower-ranked CTAs through distributed
-// shared memory to place its children, writes them, cluster barrier.
+// contiguous shares, one per CTA, each taken in chunks of BT ranks (one rank
+// per thread).  Per set:
+//   offers: every thread offers its parents' keys to their neighbours
+//           (64-bit atomicMin); cluster barrier;
+//   count:  every thread counts the neighbours whose key its parent holds,
+//           a block scan per chunk gives the CTA's total, published in
+//           shared memory; cluster barrier;
+//   place:  each CTA reads the totals of the lower-ranked CTAs through
+//           distributed shared memory and writes its children chunk by
+//           chunk in rank order (the scan of a chunk is redone here; the
+//           first chunk's counts are kept from the count pass); cluster
+//           barrier.
+// Every prefix involved (CTA totals, chunk totals, the block scan) runs in
+// rank order, so the queue is exactly the FIFO order.
 __device__ __forceinline__ unsigned long long bfs_key(int r, int slot) {
-    return ((unsigned long long)(unsigned)r << 32) | (unsigned)slot;
+    return ((unsigned long long)(unsigned)(r + 1) << 32) | (unsigned)slot;
+}
+
+// children of parent rank r (row [b, e)): count and the mask of the first 32 slots
+__device__ __forceinline__ int bfs_children(const BfsArgs &a, int r, int b, int e, unsigned &mk) {
+    int k = 0;
+    mk = 0;
+    for (int j = b; j < e; ++j) {
+        if (__ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b)) {
+            ++k;
+            if (j - b < 32) mk |= 1u << (j - b);
+        }
+    }
+    return k;
 }
 
 __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
@@ -91,62 +113,37 @@ __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
         const int per = (n + kBfsCluster - 1) / kBfsCluster;
         const int mlo = min(hi, lo + crank * per), mhi = min(hi, mlo + per);
         const int nchunk = (mhi - mlo + BT - 1) / BT;
-        int pp[kBfsChunks], rb[kBfsChunks], re[kBfsChunks];
-        // offers
-#pragma unroll
-        for (int c = 0; c < kBfsChunks; ++c) {
-            const int r = mlo + c * BT + (int)threadIdx.x;
-            int p = -1, b = 0, e = 0;
-            if (c < nchunk && r < mhi) {
-                p = __ldcg(&a.order[r]);
-                b = a.rowptr[p];
-                e = a.rowptr[p + 1];
-                for (int j = b; j < e; ++j) atomicMin(&a.key[a.col[j]], bfs_key(r, j - b));
-            }
-            pp[c] = p; rb[c] = b; re[c] = e;
-        }
-        for (int c = kBfsChunks; c < nchunk; ++c) {
+        // offers; the first chunk's row stays in registers
+        int p0 = -1, b0 = 0, e0 = 0;
+        for (int c = 0; c < nchunk; ++c) {
             const int r = mlo + c * BT + (int)threadIdx.x;
             if (r < mhi) {
                 const int p = __ldcg(&a.order[r]);
                 const int b = a.rowptr[p], e = a.rowptr[p + 1];
                 for (int j = b; j < e; ++j) atomicMin(&a.key[a.col[j]], bfs_key(r, j - b));
+                if (c == 0) { p0 = p; b0 = b; e0 = e; }
             }
         }
         cluster.sync();
-        // children per parent, scanned over this CTA's parents in rank order
-        int cnt[kBfsChunks], ex[kBfsChunks], ctot[kBfsChunks];
-        unsigned mask[kBfsChunks];
+        // count: the CTA's total over its chunks; the first chunk's counts are kept
+        int k0 = 0, ex0 = 0, tot0 = 0;
+        unsigned mk0 = 0;
         int mytotal = 0;
         for (int c = 0; c < nchunk; ++c) {
             const int r = mlo + c * BT + (int)threadIdx.x;
-            int p = -1, b = 0, e = 0;
-            if (c < kBfsChunks) {
-#pragma unroll
-                for (int x = 0; x < kBfsChunks; ++x)
-                    if (x == c) { p = pp[x]; b = rb[x]; e = re[x]; }
-            } else if (r < mhi) {
-                p = __ldcg(&a.order[r]);
-                b = a.rowptr[p];
-                e = a.rowptr[p + 1];
-            }
             int k = 0;
             unsigned mk = 0;
             if (r < mhi) {
-                for (int j = b; j < e; ++j) {
-                    if (__ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b)) {
-                        ++k;
-                        if (j - b < 32) mk |= 1u << (j - b);
-                    }
+                if (c == 0) {
+                    k = bfs_children(a, r, b0, e0, mk);
+                } else {
+                    const int p = __ldcg(&a.order[r]);
+                    k = bfs_children(a, r, a.rowptr[p], a.rowptr[p + 1], mk);
                 }
             }
             int excl;
             const int tot = bt_scan(k, excl);
-            if (c < kBfsChunks) {
-#pragma unroll
-                for (int x = 0; x < kBfsChunks; ++x)
-                    if (x == c) { cnt[x] = k; ex[x] = excl; ctot[x] = tot; mask[x] = mk; }
-            }
+            if (c == 0) { k0 = k; ex0 = excl; tot0 = tot; mk0 = mk; }
             mytotal += tot;
         }
         if (threadIdx.x == 0) s_total = mytotal;
@@ -164,33 +161,22 @@ __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
             const int r = mlo + c * BT + (int)threadIdx.x;
             int p = -1, b = 0, e = 0, k = 0, excl = 0, tot = 0;
             unsigned mk = 0;
-            if (c < kBfsChunks) {
-#pragma unroll
-                for (int x = 0; x < kBfsChunks; ++x)
-                    if (x == c) { p = pp[x]; b = rb[x]; e = re[x]; k = cnt[x]; excl = ex[x]; tot = ctot[x]; mk = mask[x]; }
+            if (c == 0) {
+                p = p0; b = b0; e = e0; k = k0; excl = ex0; tot = tot0; mk = mk0;
             } else {
-                // chunks past kBfsChunks: count again (same keys, same result) and rescan
                 if (r < mhi) {
                     p = __ldcg(&a.order[r]);
                     b = a.rowptr[p];
                     e = a.rowptr[p + 1];
-                    for (int j = b; j < e; ++j)
-                        if (__ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b)) {
-                            ++k;
-                            if (j - b < 32) mk |= 1u << (j - b);
-                        }
+                    k = bfs_children(a, r, b, e, mk);
                 }
                 tot = bt_scan(k, excl);
             }
             if (k) {
                 int at = hi + before + base_run + excl;
                 for (int j = b; j < e; ++j) {
-                    bool is_child;
-                    if (j - b < 32) {
-                        is_child = (mk >> (j - b)) & 1u;
-                    } else {
-                        is_child = __ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b);
-                    }
+                    const bool is_child = (j - b < 32) ? ((mk >> (j - b)) & 1u) != 0
+                                                       : __ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b);
                     if (is_child) {
                         const int w = a.col[j];
                         a.order[at++] = w;
@@ -238,13 +224,15 @@ __global__ void k_row_len(const int32_t *__restrict__ order, int n, const int32_
 }
 
 // row r of the level-ordered layout: neighbours renumbered to queue positions
-// with weight t*theta; idiag = 1 / (A_v + t * sum theta) (FP64, then rounded)
+// with weight t*theta; idiag = 1 / (A_v + t * sum theta) (FP64, then rounded).
+// A neighbour without a queue position would mean inconsistent breadth-first
+// sets: it is pointed at the zero slot and the status word reports it.
 template <class T>
 __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const int32_t *__restrict__ rowptr,
                               const int32_t *__restrict__ col, const int32_t *__restrict__ col_edge,
                               const double *__restrict__ theta, const double *__restrict__ Av,
                               const int32_t *__restrict__ pos, const int32_t *__restrict__ grow, double t,
-                              Ent<T> *gent, T *diag) {
+                              Ent<T> *gent, T *diag, int *status) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int v = order[r];
@@ -255,6 +243,10 @@ __global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const in
         sum += th;
         Ent<T> x;
         x.col = pos[col[j]];
+        if (x.col < 0) {   // a neighbour of a reached vertex is always reached
+            atomicCAS(status, DEV_OK, DEV_EINTERNAL);
+            x.col = n;     // the zero slot
+        }
         x.w = (T)(t * th);
         gent[o + (j - b)] = x;
     }
@@ -378,12 +370,12 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
         k_fill_layout<double><<<blocks_for(n, 256), 256, 0, st>>>(
             ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
             ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t,
-            ptr<Ent<double>>(q.gent), ptr<double>(q.diag)); ++c->launches;
+            ptr<Ent<double>>(q.gent), ptr<double>(q.diag), c->status_dev); ++c->launches;
     } else {
         k_fill_layout<float><<<blocks_for(n, 256), 256, 0, st>>>(
             ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
             ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t,
-            ptr<Ent<float>>(q.gent), ptr<float>(q.diag)); ++c->launches;
+            ptr<Ent<float>>(q.gent), ptr<float>(q.diag), c->status_dev); ++c->launches;
     }
     s = dalloc(c, q.tiles, sizeof(TileDesc) * ((size_t)n / TILE + (size_t)q.nlev + 2));
     if (s != GH_OK) return s;

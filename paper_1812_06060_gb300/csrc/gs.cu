@@ -15,13 +15,20 @@
 // tiles (it only grows, sweep after sweep).  A tile of (k, i) starts once the
 // counters show that (k, i-1), (k-1, i) and (k-1, i+1) are complete, and
 // bumps its own set's counter with a release add when done.  Tiles are
-// numbered in step order s and dealt round-robin to the CTAs serving the
-// query; every tile depends only on lower numbers, so the lowest unfinished
-// tile can always run and the kernel cannot deadlock (all CTAs are resident:
-// cooperative launch).  Each tile loads its rows (column positions, weights,
-// diagonal) before it waits, so only the gather of the neighbour state sits
-// on the dependency chain.  Several queries (right-hand sides) run in one
-// launch, each on its own group of CTAs.
+// numbered in step order s and dealt round-robin to the CTAs; every tile
+// depends only on lower numbers of its own query.  Each tile loads its rows
+// (column positions, weights, diagonal) before it waits, so only the gather
+// of the neighbour state sits on the dependency chain.
+//
+// Several queries (right-hand sides) run in one launch and every CTA serves
+// all of them: CTA c takes, for round r = 0, 1, ... and query q = 0..K-1 in
+// turn, tile r * grid + c of query q (skipping queries with fewer tiles).
+// While one query's next set waits for its predecessors, the CTA works on
+// the other queries' tiles, so the dependency latency of one wavefront is
+// filled with the work of the others.  In the order (r, q, c) every tile
+// comes after the tiles it depends on and after the earlier tiles of its
+// CTA, so the lowest unfinished tile can always run and the kernel cannot
+// deadlock (all CTAs are resident: cooperative launch).
 //
 // Vertices sit in breadth-first queue order, so D_i is a contiguous range and
 // the set of a neighbour follows from its position alone.  A tile is TILE
@@ -51,9 +58,7 @@ template <class T> struct GsJob {
     int nsteps;            // nlev + 2 (sweeps - 1)
     int n_even;            // number of even sets; ptile0[n_even] = first tile of the odd sets
     int ntickets;          // tiles over all steps
-    int cta0, ncta;        // the CTAs serving this query
     int zero_pos;          // a position that always holds the zero state (nreach)
-    int pad2;
     const int32_t *lvl_off;
     const int32_t *grow;
     const Ent<T> *gent;
@@ -70,12 +75,6 @@ __device__ __forceinline__ unsigned long long gtime() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-__device__ __forceinline__ int ld_acquire(const int32_t *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
 }
 
 __device__ __forceinline__ int ld_relaxed(const int32_t *p) {
@@ -246,14 +245,17 @@ template <class T> struct alignas(128) Stage {
     Ent<T> ent[TILE * kEntPerV + 4];
     int grow[TILE + 12];
     T diag[TILE + 8];
-    int start, count, lo, k, level, g0, d0, e0, fits, abort, finished;
+    int start, count, lo, k, level, g0, d0, e0, fits, abort, finished, q;
 };
 // every bulk-copy destination must start on a 16-byte boundary, in both stages
 static_assert(sizeof(Stage<float>) % 16 == 0 && sizeof(Stage<double>) % 16 == 0, "stage size");
 static_assert(offsetof(Stage<float>, grow) % 16 == 0 && offsetof(Stage<float>, diag) % 16 == 0, "stage layout");
 static_assert(offsetof(Stage<double>, grow) % 16 == 0 && offsetof(Stage<double>, diag) % 16 == 0, "stage layout");
 
-// tile number t of job J -> descriptor and step (t < J.ntickets)
+constexpr int kMaxJobs = 256;                 // queries per launch (larger batches take several launches)
+
+// tile number t of job J -> descriptor and step (t < J.ntickets), walking
+// forward from the step cursor scur
 template <class T>
 __device__ __forceinline__ void lookup_tile(const GsJob<T> &J, int t, int nsweeps, int &scur, TileDesc &d, int &s,
                                             int &tile) {
@@ -286,14 +288,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // sweep k once its counter reaches (k + 1) * nt.
 template <class T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
-    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nsweeps, unsigned long long wait_limit_ns, int *abort_flag,
-         int *status) {
+    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nrounds, int nsweeps, unsigned long long wait_limit_ns,
+         int *abort_flag, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage<T> *stage = reinterpret_cast<Stage<T> *>(smem_raw);
     __shared__ __align__(8) uint64_t full[2], empty[2];
-    int q = 0;
-    while (q + 1 < njobs && (int)blockIdx.x >= jobs[q + 1].cta0) ++q;
-    const GsJob<T> &J = jobs[q];
+    __shared__ int scur_job[kMaxJobs];   // producer: step cursor of each query
+    for (int q = threadIdx.x; q < njobs; q += blockDim.x) scur_job[q] = 0;
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&full[b], 1);
@@ -304,23 +305,33 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t_first = (int)blockIdx.x - J.cta0;
+    const int grid = (int)gridDim.x, cta = (int)blockIdx.x;
+    const int ncand = nrounds * njobs;   // candidates (r, q) in order; tile r * grid + cta of query q
     if (warp == 0) {
-        // Producer warp.  Lane l looks up the l-th of the next 32 tiles of this
-        // CTA (one parallel lookup per 32 tiles); lane 0 then stages, waits and
-        // releases them one by one.
+        // Producer warp.  Lane l looks up the l-th of the next 32 candidates
+        // (one parallel lookup per 32); lane 0 then stages, waits and releases
+        // the valid ones one by one.
         constexpr int EA = 16 / (int)sizeof(Ent<T>);   // entries per 16 bytes
         constexpr int DA = 16 / (int)sizeof(T);        // diagonal values per 16 bytes
-        int scur = 0;
         uint32_t eph[2] = {0u, 0u};
         int j = 0;
-        for (int base = t_first; base < J.ntickets; base += 32 * J.ncta) {
-            const int tl = base + lane * J.ncta;
+        for (int base = 0; base < ncand; base += 32) {
+            const int cl = base + lane;
+            const int ql = (cl < ncand) ? cl % njobs : 0;
+            const int tl = (cl / njobs) * grid + cta;
+            const bool vl = cl < ncand && tl < jobs[ql].ntickets;
             TileDesc dl{};
             int sl = 0, tidl = 0;
-            if (tl < J.ntickets) lookup_tile(J, tl, nsweeps, scur, dl, sl, tidl);
-            const int nwin = min(32, (J.ntickets - base + J.ncta - 1) / J.ncta);
-            for (int w = 0; w < nwin; ++w, ++j) {
+            if (vl) {
+                int sc = scur_job[ql];
+                lookup_tile(jobs[ql], tl, nsweeps, sc, dl, sl, tidl);
+                atomicMax_block(&scur_job[ql], sc);   // the lane with the last tile of q sets it
+            }
+            __syncwarp();
+            const unsigned vmask = __ballot_sync(0xffffffffu, vl);
+            const int nwin = min(32, ncand - base);
+            for (int w = 0; w < nwin; ++w) {
+                if (!((vmask >> w) & 1u)) continue;
                 TileDesc d;
                 d.level = __shfl_sync(0xffffffffu, dl.level, w);
                 d.start = __shfl_sync(0xffffffffu, dl.start, w);
@@ -333,6 +344,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                 d.nt_next = __shfl_sync(0xffffffffu, dl.nt_next, w);
                 const int s = __shfl_sync(0xffffffffu, sl, w);
                 const int tile = __shfl_sync(0xffffffffu, tidl, w);
+                const int q = __shfl_sync(0xffffffffu, ql, w);
+                const GsJob<T> &J = jobs[q];
+                (void)tile;
                 int ok = 1;
                 if (lane == 0) {
                     const int b = j & 1;
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                         if (be) bulk_g2s(S.ent, J.gent + e0, be, &full[b]);
                         const int i = d.level, k = (s - d.level) >> 1;
                         S.start = d.start; S.count = d.count; S.lo = d.lo; S.k = k; S.level = i;
-                        S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits;
+                        S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits; S.q = q;
                         // predecessors: (k, i-1), (k-1, i), (k-1, i+1)
                         const int t0 = (i > 0) ? (k + 1) * d.nt_prev : 0;
                         const int t1 = (k > 0) ? k * d.nt_self : 0;
@@ -372,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) return;
+                ++j;
             }
         }
         return;
@@ -380,8 +395,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
     const int cw = warp - 1;
     uint32_t fph[2] = {0u, 0u};
     int j = 0;
-    for (int t = t_first; t < J.ntickets; t += J.ncta, ++j) {
+    for (int cand = 0; cand < ncand; ++cand) {
+        if ((cand / njobs) * grid + cta >= jobs[cand % njobs].ntickets) continue;
         const int b = j & 1;
+        ++j;
         Stage<T> &S = stage[b];
         if (!mbar_wait_bounded(&full[b], fph[b], abort_flag)) {
             if (lane == 0) {
@@ -395,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         const int start = S.start, count = S.count, lo = S.lo, k = S.k, level = S.level;
         const int sg = S.g0, sd = S.d0, se = S.e0;
         const bool fits = S.fits != 0;
+        const GsJob<T> &J = jobs[S.q];
         XVal<T> *Ucur = J.U[k & 1];
         const XVal<T> *Uprv = J.U[(k & 1) ^ 1];
         int rb[kVPT], re[kVPT];
@@ -473,8 +491,19 @@ template <class T> __global__ void k_zero_state(XVal<T> *a, XVal<T> *b, int n) {
     }
 }
 
-template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sweeps, cudaEvent_t ev0,
+template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, int sweeps, cudaEvent_t ev0,
                                      cudaEvent_t ev1) {
+    if ((int)all_ws.size() > kMaxJobs) {   // one launch per kMaxJobs queries
+        for (size_t b = 0; b < all_ws.size(); b += kMaxJobs) {
+            std::vector<QueryWs *> part(all_ws.begin() + b,
+                                        all_ws.begin() + std::min(all_ws.size(), b + (size_t)kMaxJobs));
+            gh_status s = run_gs_t<T>(c, part, sweeps, b == 0 ? ev0 : nullptr,
+                                      b + kMaxJobs >= all_ws.size() ? ev1 : nullptr);
+            if (s != GH_OK) return s;
+        }
+        return GH_OK;
+    }
+    std::vector<QueryWs *> &ws = all_ws;
     cudaStream_t st = c->stream;
     const int K = (int)ws.size();
     int per_sm = 0;
@@ -483,7 +512,6 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs<T>, kThreads, smem));
     if (per_sm < 1) { set_error("diffusion kernel does not fit on an SM"); return GH_EDEVICE; }
     const int grid = std::max(1, per_sm * c->num_sms / std::max(1, c->gs_share));
-    if (K > grid) { set_error("internal: more queries than resident CTAs in one diffusion launch"); return GH_EINVAL; }
     std::vector<GsJob<T>> jobs(K);
     size_t soff_total = 0;
     for (int q = 0; q < K; ++q) soff_total += (size_t)ws[q]->nlev + 2 * (size_t)sweeps + 2;
@@ -492,16 +520,12 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     GsJob<T> *djobs = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&djobs, sizeof(GsJob<T>) * K, st));
     size_t at = 0;
-    int cta = 0;
     for (int q = 0; q < K; ++q) {
         QueryWs &w = *ws[q];
         GsJob<T> j{};
         j.nlev = w.nlev;
         j.nsteps = w.nlev + 2 * (sweeps - 1);
         j.n_even = (w.nlev + 1) / 2;
-        j.cta0 = cta;
-        j.ncta = grid / K + (q < grid % K ? 1 : 0);
-        cta += j.ncta;
         j.lvl_off = ptr<int32_t>(w.lvl_off);
         j.grow = ptr<int32_t>(w.grow);
         j.gent = ptr<Ent<T>>(w.gent);
@@ -534,11 +558,14 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &ws, int sw
     GH_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(GsJob<T>) * K, cudaMemcpyHostToDevice, st));
     GH_CUDA(cudaMemsetAsync(&c->bar_dev->abort, 0, sizeof(int), st));
     int njobs = K;
+    int maxtick = 0;
+    for (int q = 0; q < K; ++q) maxtick = std::max(maxtick, ntick[q]);
+    int nrounds = (maxtick + grid - 1) / grid;
     int *status = c->status_dev;
     int *abort_flag = &c->bar_dev->abort;
     unsigned long long wait_limit_ns = c->wait_limit_ns;
-    void *argv[] = {(void *)&djobs, (void *)&njobs, (void *)&sweeps, (void *)&wait_limit_ns, (void *)&abort_flag,
-                    (void *)&status};
+    void *argv[] = {(void *)&djobs,         (void *)&njobs,      (void *)&nrounds, (void *)&sweeps,
+                    (void *)&wait_limit_ns, (void *)&abort_flag, (void *)&status};
     if (ev0) cudaEventRecord(ev0, st);
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_gs<T>, dim3(grid), dim3(kThreads), argv, smem, st);
     ++c->launches;

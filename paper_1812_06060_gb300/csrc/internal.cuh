@@ -20,6 +20,7 @@ enum DevErr : int {
     DEV_EINVAL = 1,
     DEV_ENONMANIFOLD = 2,
     DEV_ETIMEOUT = 3,
+    DEV_EINTERNAL = 4,   // an internal consistency check failed (the access was redirected, not made)
 };
 
 void set_error(const std::string &msg);

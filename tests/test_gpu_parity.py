@@ -180,6 +180,58 @@ def test_small_odd_grid_and_two_components(gh, ctx):
     r["M"].close()
 
 
+def _chunks_per_cta(level):
+    """Parent chunks (1024 ranks) per CTA of the 8-CTA cluster for the widest set."""
+    widest = int(np.bincount(level[level >= 0]).max())
+    return ((widest + 7) // 8 + 1023) // 1024
+
+
+@pytest.mark.parametrize("nx,step", [(5000, 2), (10000, 2), (17000, 2), (50000, 2), (3000, 1)])
+def test_wide_sets_bfs_exact(gh, ctx, nx, step):
+    """Breadth-first sets far wider than one block of the cluster: every CTA
+    takes its share of a set in several chunks (up to 10 here).  step 1 puts
+    adjacent vertices in the source set, so a source is the first neighbour
+    of the lowest-ranked source.  Sets, pairing, queue order: bit-exact."""
+    mesh = meshgen.strip_grid(nx, 6)
+    src = np.arange(0, nx, step, dtype=np.int32)
+    md = oracle.mesh_data(mesh.V, mesh.F)
+    ref = oracle.bfs(md, src)
+    if step == 2:
+        assert _chunks_per_cta(ref.level) == {5000: 1, 10000: 2, 17000: 4, 50000: 10}[nx]
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    try:
+        out = np.empty(md.nv)
+        M.solve(src, out, gh.params(gs_sweeps=2, admm_iters=1, form="edge"))
+        assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL), ref.level)
+        assert np.array_equal(M.dump(gh.GH_DUMP_PARENT), ref.parent)
+        assert np.array_equal(M.dump(gh.GH_DUMP_ORDER), ref.order)
+        assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL_OFF), ref.level_off)
+        assert np.all(np.isfinite(out))
+    finally:
+        M.close()
+
+
+def test_wide_sets_batch(gh, ctx):
+    """Several wide-front queries in one batch (one cluster each): each
+    query's sets and order equal the oracle's."""
+    nx = 17000
+    mesh = meshgen.strip_grid(nx, 5)
+    md = oracle.mesh_data(mesh.V, mesh.F)
+    sets = [np.arange(0, nx, 2, dtype=np.int32), np.arange(1, nx, 2, dtype=np.int32),
+            np.arange(0, nx, 1, dtype=np.int32), np.array([nx // 2], np.int32)]
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    try:
+        out = np.empty((len(sets), md.nv))
+        M.solve_batch(sets, out, gh.params(gs_sweeps=2, admm_iters=1, form="face"))
+        for q, s_ in enumerate(sets):
+            ref = oracle.bfs(md, s_)
+            assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL, q), ref.level), q
+            assert np.array_equal(M.dump(gh.GH_DUMP_PARENT, q), ref.parent), q
+            assert np.array_equal(M.dump(gh.GH_DUMP_ORDER, q), ref.order), q
+    finally:
+        M.close()
+
+
 def test_batch_equals_single_solves(gh, ctx):
     m = meshgen.noisy_icosphere(4, 8)
     rng = meshgen.rng_for(5)
