@@ -145,6 +145,42 @@ def gs_bytes(nv: int, ne: int, sweeps: int) -> int:
     return sweeps * (24 * nv + 8 * 2 * ne)
 
 
+STAGES = ("bfs_layout", "diffusion", "normalize", "admm", "integrate")
+
+
+def stage_bytes(nv: int, ne: int, nf: int, sweeps: int, iters: int, form: str, nlev: int) -> dict:
+    """Algorithmic bytes of each stage of one FP32 solve: every array a stage
+    must read or write, counted once (entries = 2 ne directed edges).
+      breadth-first sets + layout: 88 per vertex (row pointers, queue, set,
+        pairing, position, row length, scan, diagonal) + 52 per entry
+        (offer and count reads of the column, the key atomic and read, and the
+        layout's column, edge id, theta, position and the written entry)
+      diffusion: see gs_bytes
+      normalise: 66 per face (face, positions, state, gradient operator, h)
+      face ADMM: 60 per face to initialise, 154 per face and iteration (g, lambda
+        read and written, h, face edges, twins, area, edge vectors)
+      edge ADMM: 78 per face + 32 per edge to initialise, per iteration 69 per
+        face (face pass: x, lambda, w, signs) + 44 per edge (edge pass)
+      integration: 64 (edge form) or 112 (face form) per vertex for the
+        increments, 36 per vertex for each of ceil(log2 L) jumping rounds"""
+    import math
+    rows = 2 * ne
+    adm = (60 * nf + iters * 154 * nf) if form == "face" else (78 * nf + 32 * ne + iters * (69 * nf + 44 * ne))
+    rounds = max(1, math.ceil(math.log2(max(nlev, 2))))
+    return {"bfs_layout": 88 * nv + 52 * rows, "diffusion": gs_bytes(nv, ne, sweeps), "normalize": 66 * nf,
+            "admm": adm, "integrate": (64 if form == "edge" else 112) * nv + 36 * nv * rounds}
+
+
+def stage_roofline(stage_ms, nbytes, peak):
+    """Achieved GB/s of each stage against the HBM peak."""
+    out = {}
+    for i, k in enumerate(STAGES):
+        ms = float(stage_ms[i])
+        gbps = nbytes[k] / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+        out[k] = {"bytes": int(nbytes[k]), "ms": round(ms, 4), "GBps": round(gbps, 1), "frac": round(gbps / peak, 3)}
+    return out
+
+
 def gs_traffic():
     """DRAM bytes per diffusion launch from the committed ncu capture, if it
     was taken on the current kernel source."""
@@ -412,6 +448,17 @@ def run_ours(args):
         serve = serve_summary(g, local, sm, 120, 1.0, meshgen.config_seed(4, 100))
 
     peak, peak_kind = measured_peaks()
+    # every stage of one solve of each form (untimed, after the timed region)
+    stages = None
+    if rank == 0:
+        nlev = len(M.dump(g.GH_DUMP_LEVEL_OFF)) - 1
+        stages = {}
+        for f in FORMS:
+            flush.zero_()
+            M.solve(src, out[f], prm[f])
+            torch.cuda.synchronize()
+            stages[f] = stage_roofline(M.stage_times(), stage_bytes(mesh.nv, M.ne, mesh.nf, SWEEPS, ADMM, f, nlev),
+                                       peak)
     bytes_launch = gs_bytes(mesh.nv, M.ne, SWEEPS)
     gs_avg_ms = statistics.mean(gs_ms)
     achieved = bytes_launch / (gs_avg_ms / 1000.0) / 1e9
@@ -435,6 +482,9 @@ def run_ours(args):
                                  "from L2, so the HBM fraction can exceed 1"},
             "stage_ms_last_solve": dict(zip(["bfs_layout", "diffusion", "normalize", "admm", "integrate",
                                              "k_gs"], [round(x, 4) for x in M.stage_times()])),
+            "stage_roofline": {"peak_GBps": peak, "by_form": stages,
+                               "note": "algorithmic bytes per stage (each array once) / CUDA-event stage time; "
+                                       "the breadth-first stage is bound by its L dependent set steps, not HBM"},
             "clocks": clk.summary(),
             "batch": batch,
             "serve": serve,
@@ -508,6 +558,11 @@ def run_workload(args):
                     "gs_vertex_updates_per_s_batch": K * sweeps * V / (stb[5] / 1000.0),
                     "gs_algorithmic_GBps_batch": K * gs_bytes(V, M.ne, sweeps) / (stb[5] / 1000.0) / 1e9,
                     "device_bytes": ctx.memory()})
+        peak, _ = measured_peaks()
+        nlev1 = len(M.dump(g.GH_DUMP_LEVEL_OFF, K - 1)) - 1
+        sb = stage_bytes(V, M.ne, w.mesh.nf, sweeps, 10, form, nlev1)
+        out["stage_roofline_single"] = stage_roofline(st1, sb, peak)
+        out["stage_roofline_batch"] = stage_roofline(stb, {k: K * v for k, v in sb.items()}, peak)
         d = dout.cpu().numpy()
         out["finite_fraction"] = float(np.isfinite(d).mean())
         M.close()
@@ -552,6 +607,9 @@ def run_workload(args):
                     "finite_fraction": float(np.isfinite(dh).mean()),
                     "min_d_over_chord": float(np.min(dh[chord > 0] / chord[chord > 0])),
                     "max_d": float(np.max(dh))})
+        peak, _ = measured_peaks()
+        nlev = len(M.dump(g.GH_DUMP_LEVEL_OFF)) - 1
+        out["stage_roofline"] = stage_roofline(st, stage_bytes(V, M.ne, w.mesh.nf, w.gs_edge, 10, "edge", nlev), peak)
         M.close()
         ctx.close()
     print(json.dumps(out), flush=True)

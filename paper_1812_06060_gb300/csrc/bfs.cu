@@ -23,8 +23,10 @@ constexpr int BT = 1024;
 struct BfsArgs {
     const int32_t *rowptr;
     const int32_t *col;
+    const int32_t *col_edge;
     int32_t *level;
     int32_t *parent;
+    int32_t *pedge;
     int32_t *order;
     unsigned long long *key;
     int32_t *lvl_off;
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
                         a.order[at++] = w;
                         a.level[w] = nlev;
                         a.parent[w] = p;
+                        a.pedge[w] = a.col_edge[j];
                     }
                 }
             }
@@ -316,8 +319,8 @@ gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const st
         GH_CUDA(cudaMemcpyAsync(w.order.p, src[q].data(), sizeof(int32_t) * src[q].size(), cudaMemcpyHostToDevice, st));
         k_seed<<<blocks_for((int64_t)src[q].size(), 256), 256, 0, st>>>(ptr<int32_t>(w.level), ptr<unsigned long long>(w.key), ptr<int32_t>(w.order),
                                                                        (int)src[q].size()); ++c->launches;
-        args[q] = BfsArgs{ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(w.level), ptr<int32_t>(w.parent),
-                          ptr<int32_t>(w.order), ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off),
+        args[q] = BfsArgs{ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge), ptr<int32_t>(w.level),
+                          ptr<int32_t>(w.parent), ptr<int32_t>(w.pedge), ptr<int32_t>(w.order), ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off),
                           ptr<int32_t>(w.meta), (int32_t)src[q].size()};
     }
     BfsArgs *dargs = nullptr;

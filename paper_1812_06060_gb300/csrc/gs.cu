@@ -83,7 +83,8 @@ __device__ __forceinline__ int ld_relaxed(const int32_t *p) {
     return v;
 }
 
-__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// the acquire half of a relaxed poll: later loads see what the observed release published
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acquire.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ void red_release_add(int32_t *p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -351,6 +352,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                 if (lane == 0) {
                     const int b = j & 1;
                     Stage<T> &S = stage[b];
+                    // predecessors: (k, i-1), (k-1, i), (k-1, i+1); their counters are
+                    // read now, so the loads are in flight while the buffer frees up
+                    const int i = d.level, k = (s - d.level) >> 1;
+                    const int t0 = (i > 0) ? (k + 1) * d.nt_prev : 0;
+                    const int t1 = (k > 0) ? k * d.nt_self : 0;
+                    const int t2 = (k > 0) ? k * d.nt_next : 0;
+                    const int32_t *c0 = J.done + (i > 0 ? i - 1 : 0), *c1 = J.done + i, *c2 = J.done + i + 1;
+                    const int pv0 = (t0 > 0) ? ld_relaxed(c0) : 0;
+                    const int pv1 = (t1 > 0) ? ld_relaxed(c1) : 0;
+                    const int pv2 = (t2 > 0) ? ld_relaxed(c2) : 0;
                     if (j >= 2) {
                         if (!mbar_wait_bounded(&empty[b], eph[b], abort_flag)) {
                             atomicExch(abort_flag, 1);
@@ -371,15 +382,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                         bulk_g2s(S.grow, J.grow + g0, bg, &full[b]);
                         bulk_g2s(S.diag, J.diag + d0, bd, &full[b]);
                         if (be) bulk_g2s(S.ent, J.gent + e0, be, &full[b]);
-                        const int i = d.level, k = (s - d.level) >> 1;
                         S.start = d.start; S.count = d.count; S.lo = d.lo; S.k = k; S.level = i;
                         S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits; S.q = q;
-                        // predecessors: (k, i-1), (k-1, i), (k-1, i+1)
-                        const int t0 = (i > 0) ? (k + 1) * d.nt_prev : 0;
-                        const int t1 = (k > 0) ? k * d.nt_self : 0;
-                        const int t2 = (k > 0) ? k * d.nt_next : 0;
-                        ok = wait_sets(J.done + (i > 0 ? i - 1 : 0), t0, J.done + i, t1, J.done + i + 1, t2,
-                                       wait_limit_ns, abort_flag, status) ? 1 : 0;
+                        if (pv0 >= t0 && pv1 >= t1 && pv2 >= t2)
+                            fence_acquire();
+                        else
+                            ok = wait_sets(c0, t0, c1, t1, c2, t2, wait_limit_ns, abort_flag, status) ? 1 : 0;
                         S.abort = ok ? 0 : 1;
                         mbar_arrive(&full[b]);
                     }

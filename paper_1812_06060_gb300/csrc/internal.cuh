@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -135,6 +137,11 @@ struct DevMesh {
     DBuf ev;         // float [ne*3] edge vector max - min (orientation halfedge)
     DBuf gradop;     // float [nf*9] grad of corner k's hat function: (N x e_k)/(2A)
     DBuf Aff;        // float [nf] face area
+    // face-form ADMM: per face, for slots k = 0..2 the unit edge vector and the
+    // twin weight A'/(A + A'), then sqrt(A_f): 16 values (FP32 and FP64
+    // copies), built on the first face-form solve
+    DBuf face_rec32, face_rec64;
+    std::shared_ptr<std::mutex> rec_mu = std::make_shared<std::mutex>();
 };
 
 // Per-query workspace (BFS products, the level-ordered layout, solver state).
@@ -143,6 +150,7 @@ struct QueryWs {
     int fp64 = 0;
     // breadth-first traversal
     DBuf level, parent, order, pos, key, lvl_off, meta;  // meta: [0] nlev [1] nreach [2] err
+    DBuf pedge;     // int32 [nv] edge from each vertex to its pairing vertex
     // level-ordered Gauss-Seidel layout
     DBuf grow;      // int32 [nv+1] (+ padding for aligned bulk copies)
     DBuf gent;      // Ent<T> [2ne] (+ padding)
@@ -153,7 +161,7 @@ struct QueryWs {
     // stages
     DBuf h;         // T [nf*3]
     DBuf g0, g1;    // T [nf*3] face form
-    DBuf l0, l1;    // T [nf*9] face form dual per slot
+    DBuf l0, l1;    // T [nf*9] face form: per slot q_k = g - lambda_k / (mu alpha)
     DBuf z, w, lam; // T [nf*3] edge form
     DBuf sz, x;     // T [ne] edge form
     DBuf inc;       // double [nv]
@@ -208,7 +216,7 @@ gh_status run_gs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, int sweep
 
 // stages.cu
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q);
-gh_status run_face_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu);
+gh_status run_face_admm(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu);
 gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu);
 gh_status run_integrate(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out_dev);
 gh_status run_heat_residual(Ctx *c, const DevMesh &m, QueryWs &q);

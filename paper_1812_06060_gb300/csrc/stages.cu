@@ -92,68 +92,98 @@ __global__ void k_normalize(int64_t nf, const int32_t *__restrict__ F, const int
 
 // ------------------------------------------------------------------ face ADMM
 
-// One ADMM iteration per face (Y, G, lambda in the paper's order), reading
-// the previous iteration's g and lambda of the face and of its neighbours
-// across interior edges (buffers *_in) and writing the new ones (*_out).
-//   q = g - lambda/(mu alpha);  y = q + A'/(A + A') ebar (ebar . (q' - q))
-//   g = (2h + mu sum_k (y_k + lambda_k/(mu alpha))) / (2 + mu n)
-//   lambda_k += mu alpha (y_k - g)
-// Optional residual partials per block: [0] |alpha (y - g)|^2,
-// [1] |mu alpha (g - g_old)|^2 summed over interior slots.
+// Static per-face data of the face form (FP64 arithmetic, stored as T):
+// rec[16 f + 4 k + c] the unit vector of the edge opposite corner k (c < 3)
+// and rec[16 f + 4 k + 3] the twin weight A'/(A + A') (0 on a boundary
+// slot); rec[16 f + 12] = alpha = sqrt(A_f).
 template <class T>
-__global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ face_edge,
-                                                  const int32_t *__restrict__ twin, Geo<T> geo, const T *__restrict__ h,
-                                                  const T *__restrict__ g_in, const T *__restrict__ l_in, T *g_out,
-                                                  T *l_out, T mu, double *part) {
+__global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32_t *__restrict__ edges,
+                           const int32_t *__restrict__ face_edge, const int32_t *__restrict__ twin,
+                           const double *__restrict__ Af, T *rec) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const double A = Af[f];
+    T *o = rec + 16 * f;
+    for (int k = 0; k < 3; ++k) {
+        const int e = face_edge[3 * f + k];
+        const double *a = P + 3 * edges[2 * e], *b = P + 3 * edges[2 * e + 1];
+        const double v[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double il = 1.0 / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const int tw = twin[3 * f + k];
+        const double A2 = (tw >= 0) ? Af[tw >> 2] : 0.0;
+        o[4 * k] = (T)(v[0] * il);
+        o[4 * k + 1] = (T)(v[1] * il);
+        o[4 * k + 2] = (T)(v[2] * il);
+        o[4 * k + 3] = (T)((tw >= 0) ? A2 / (A + A2) : 0.0);
+    }
+    o[12] = (T)sqrt(A);
+    o[13] = o[14] = o[15] = T(0);
+}
+
+// four values loaded as one vector (16 bytes in FP32, 32 in FP64)
+template <class T> struct alignas(4 * sizeof(T)) Quad { T x, y, z, w; };
+
+// One ADMM iteration per face, Y then G then lambda (Sec. 3.2), with the
+// multiplier of slot k carried as q_k = g - lambda_k/(mu alpha) (the Y
+// subproblem's input; lambda_k/(mu alpha) = g - q_k):
+//   y_k = q_k + A'/(A + A') ebar (ebar . (q'_k - q_k))   (q' of the twin slot)
+//   g'  = (2h + mu sum_k (y_k + g - q_k)) / (2 + mu n)
+//   lambda_k += mu alpha (y_k - g')  <=>  q_k' = 2g' - g + q_k - y_k
+// over the n interior slots; the twins' q are the previous iteration's
+// (buffers *_in), the new g and q go to *_out.
+// Optional residual partials per block: [0] |alpha (y - g')|^2,
+// [1] |mu alpha (g' - g)|^2 summed over interior slots.
+template <class T>
+__global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ twin,
+                                                  const T *__restrict__ rec, const T *__restrict__ h,
+                                                  const T *__restrict__ g_in, const T *__restrict__ q_in, T *g_out,
+                                                  T *q_out, T mu, double *part) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
     if (f < nf) {
-        const T A = geo.area(f);
-        const T alpha = sqrt_t<T>(A);
-        T g[3] = {g_in[3 * f], g_in[3 * f + 1], g_in[3 * f + 2]};
-        T y[3][3], lam[3][3];
+        const Quad<T> *r4 = reinterpret_cast<const Quad<T> *>(rec + 16 * f);
+        const Quad<T> ek[3] = {r4[0], r4[1], r4[2]};
+        const T alpha = r4[3].x;
+        T g[3], q[3][3], y[3][3];
         bool in[3];
+        for (int c = 0; c < 3; ++c) g[c] = g_in[3 * f + c];
         T acc[3] = {0, 0, 0};
         int n = 0;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            for (int c = 0; c < 3; ++c) lam[k][c] = l_in[9 * f + 3 * k + c];
-            int tw = twin[3 * f + k];
+            for (int c = 0; c < 3; ++c) q[k][c] = q_in[9 * f + 3 * k + c];
+            const int tw = twin[3 * f + k];
             in[k] = tw >= 0;
             if (!in[k]) continue;
-            int f2 = tw >> 2, k2 = tw & 3;
-            T A2 = geo.area(f2);
-            T a2 = sqrt_t<T>(A2);
-            T ev[3];
-            geo.edge(face_edge[3 * f + k], ev);
-            T il = T(1) / sqrt_t<T>(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
-            T eb[3] = {ev[0] * il, ev[1] * il, ev[2] * il};
-            T q[3], q2[3];
+            const T *qt = q_in + 9 * (int64_t)(tw >> 2) + 3 * (tw & 3);
+            const T eb[3] = {ek[k].x, ek[k].y, ek[k].z};
+            const T proj = eb[0] * (qt[0] - q[k][0]) + eb[1] * (qt[1] - q[k][1]) + eb[2] * (qt[2] - q[k][2]);
             for (int c = 0; c < 3; ++c) {
-                q[c] = g[c] - lam[k][c] / (mu * alpha);
-                q2[c] = g_in[3 * f2 + c] - l_in[9 * f2 + 3 * k2 + c] / (mu * a2);
-            }
-            T proj = eb[0] * (q2[0] - q[0]) + eb[1] * (q2[1] - q[1]) + eb[2] * (q2[2] - q[2]);
-            T wgt = A2 / (A + A2);
-            for (int c = 0; c < 3; ++c) {
-                y[k][c] = q[c] + wgt * eb[c] * proj;
-                acc[c] += y[k][c] + lam[k][c] / (mu * alpha);
+                y[k][c] = q[k][c] + ek[k].w * eb[c] * proj;
+                acc[c] += y[k][c] + (g[c] - q[k][c]);
             }
             ++n;
         }
         T gn[3];
-        for (int c = 0; c < 3; ++c) gn[c] = (T(2) * h[3 * f + c] + mu * acc[c]) / (T(2) + mu * T(n));
-        for (int c = 0; c < 3; ++c) g_out[3 * f + c] = gn[c];
+        const T den = T(2) + mu * T(n);
+        for (int c = 0; c < 3; ++c) {
+            gn[c] = (T(2) * h[3 * f + c] + mu * acc[c]) / den;
+            g_out[3 * f + c] = gn[c];
+        }
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
             for (int c = 0; c < 3; ++c) {
-                T lk = lam[k][c];
+                T qn = gn[c];
                 if (in[k]) {
-                    T r = alpha * (y[k][c] - gn[c]);
-                    lk += mu * r;
-                    rp += (double)r * (double)r;
-                    double dgv = (double)mu * (double)alpha * ((double)gn[c] - (double)g[c]);
-                    rd += dgv * dgv;
+                    qn = T(2) * gn[c] - g[c] + q[k][c] - y[k][c];
+                    if (part) {   // residual norms only when asked for (FP64 arithmetic is slow here)
+                        const T r = alpha * (y[k][c] - gn[c]);
+                        rp += (double)r * (double)r;
+                        const double dgv = (double)mu * (double)alpha * ((double)gn[c] - (double)g[c]);
+                        rd += dgv * dgv;
+                    }
                 }
-                l_out[9 * f + 3 * k + c] = lk;
+                q_out[9 * f + 3 * k + c] = qn;
             }
         }
     }
@@ -170,12 +200,18 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
     }
 }
 
+// g = h, lambda = 0 (q = g on every slot)
 template <class T>
-__global__ void k_face_init(int64_t nf, const T *__restrict__ h, T *g, T *l) {
+__global__ void k_face_init(int64_t nf, const T *__restrict__ h, T *g, T *q) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
-    for (int c = 0; c < 3; ++c) g[3 * f + c] = h[3 * f + c];
-    for (int c = 0; c < 9; ++c) l[9 * f + c] = T(0);
+    for (int c = 0; c < 3; ++c) {
+        const T v = h[3 * f + c];
+        g[3 * f + c] = v;
+        q[9 * f + c] = v;
+        q[9 * f + 3 + c] = v;
+        q[9 * f + 6 + c] = v;
+    }
 }
 
 // ------------------------------------------------------------------ edge ADMM
@@ -302,23 +338,12 @@ __global__ void k_resid_final(const double *__restrict__ part, int nblocks, doub
 
 // ------------------------------------------------------------------ integration
 
-__device__ __forceinline__ int find_in_row(const int32_t *__restrict__ col, int b, int e, int x) {
-    while (b < e) {
-        int m = (b + e) >> 1;
-        int c = col[m];
-        if (c == x) return m;
-        if (c < x) b = m + 1; else e = m;
-    }
-    return -1;
-}
-
 // increment of each vertex over its breadth-first pairing vertex k:
 // face form  1/|T| sum_{f in T_jk} g_f . (p_j - p_k)   (eq. IntegrationStep)
 // edge form  +x_e if v_j is the head of the orientation halfedge, else -x_e
 template <class T>
 __global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, const int32_t *__restrict__ parent,
-                             const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                             const int32_t *__restrict__ col_edge, const int32_t *__restrict__ edges,
+                             const int32_t *__restrict__ pedge, const int32_t *__restrict__ edges,
                              const int32_t *__restrict__ edge_face, const double *__restrict__ P,
                              const T *__restrict__ g, const T *__restrict__ x, int form, double *inc, int32_t *nxt,
                              double *d) {
@@ -331,15 +356,8 @@ __global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, cons
         d[v] = (lv == 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
         return;
     }
-    int p = parent[v];
-    int j = find_in_row(col, rowptr[v], rowptr[v + 1], p);
-    if (j < 0) {  // cannot happen for a breadth-first pairing; keeps the access in bounds
-        inc[v] = 0.0;
-        nxt[v] = -1;
-        d[v] = __longlong_as_double(0x7ff8000000000000ll);
-        return;
-    }
-    int e = col_edge[j];
+    const int p = parent[v];
+    const int e = pedge[v];   // the edge (v, p), recorded by the breadth-first traversal
     double dv;
     if (form == GH_FORM_EDGE) {
         double xe = (double)x[e];
@@ -419,19 +437,39 @@ template <class T> gh_status normalize_t(Ctx *c, const DevMesh &m, QueryWs &q) {
     return GH_OK;
 }
 
-template <class T> gh_status face_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+// the mesh's static face-form data, built once (under the mesh's lock, and
+// finished before any solve may use it)
+template <class T> gh_status face_rec(Ctx *c, DevMesh &m, const T *&out) {
+    DBuf &buf = sizeof(T) == 4 ? m.face_rec32 : m.face_rec64;
+    std::lock_guard<std::mutex> lk(*m.rec_mu);
+    if (!buf.p) {
+        gh_status s = dalloc(c, buf, sizeof(T) * 16 * (size_t)m.nf);
+        if (s != GH_OK) return s;
+        k_face_rec<T><<<blocks_for(m.nf, NT), NT, 0, c->stream>>>(m.nf, ptr<double>(m.P), ptr<int32_t>(m.edges),
+                                                                 ptr<int32_t>(m.face_edge), ptr<int32_t>(m.twin),
+                                                                 ptr<double>(m.Af), ptr<T>(buf)); ++c->launches;
+        GH_CUDA(cudaGetLastError());
+        GH_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    out = ptr<T>(buf);
+    return GH_OK;
+}
+
+template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu) {
     cudaStream_t st = c->stream;
     unsigned nb = blocks_for(m.nf, NT);
+    const T *rec = nullptr;
+    gh_status s = face_rec<T>(c, m, rec);
+    if (s != GH_OK) return s;
     T *g[2] = {ptr<T>(q.g0), ptr<T>(q.g1)};
-    T *l[2] = {ptr<T>(q.l0), ptr<T>(q.l1)};
-    k_face_init<T><<<nb, NT, 0, st>>>(m.nf, ptr<T>(q.h), g[0], l[0]); ++c->launches;
+    T *qq[2] = {ptr<T>(q.l0), ptr<T>(q.l1)};   // the q_k of each slot
+    k_face_init<T><<<nb, NT, 0, st>>>(m.nf, ptr<T>(q.h), g[0], qq[0]); ++c->launches;
     double *part = nullptr;
     if (q.diagnostics) GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
-    Geo<T> geo = make_geo<T>(m);
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;
-        k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), ptr<int32_t>(m.twin), geo, ptr<T>(q.h),
-                                          g[a], l[a], g[a ^ 1], l[a ^ 1], (T)mu, part); ++c->launches;
+        k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1],
+                                          qq[a ^ 1], (T)mu, part); ++c->launches;
         if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it); ++c->launches; }
     }
     if (part) cudaFreeAsync(part, st);
@@ -468,8 +506,8 @@ template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, d
     unsigned nb = blocks_for(m.nv, NT);
     double *d[2] = {ptr<double>(q.d0), ptr<double>(q.d1)};
     int32_t *n[2] = {ptr<int32_t>(q.n0), ptr<int32_t>(q.n1)};
-    k_increments<T><<<nb, NT, 0, st>>>(m.nv, ptr<int32_t>(q.level), ptr<int32_t>(q.parent), ptr<int32_t>(m.rowptr),
-                                       ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge), ptr<int32_t>(m.edges),
+    k_increments<T><<<nb, NT, 0, st>>>(m.nv, ptr<int32_t>(q.level), ptr<int32_t>(q.parent), ptr<int32_t>(q.pedge),
+                                       ptr<int32_t>(m.edges),
                                        ptr<int32_t>(m.edge_face), ptr<double>(m.P), ptr<T>(q.g0), ptr<T>(q.x), q.form,
                                        ptr<double>(q.inc), n[0], d[0]); ++c->launches;
     int rounds = 0;
@@ -509,7 +547,7 @@ template <class T> gh_status heat_resid_t(Ctx *c, QueryWs &q) {
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q) {
     return q.fp64 ? normalize_t<double>(c, m, q) : normalize_t<float>(c, m, q);
 }
-gh_status run_face_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+gh_status run_face_admm(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu) {
     q.form = GH_FORM_FACE;
     gh_status s = q.fp64 ? face_admm_t<double>(c, m, q, iters, mu) : face_admm_t<float>(c, m, q, iters, mu);
     if (s != GH_OK) return s;
