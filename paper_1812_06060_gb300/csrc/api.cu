@@ -104,7 +104,7 @@ bool is_device_ptr(const void *p) {
 }
 
 void free_ws(Ctx *c, QueryWs *w) {
-    DBuf *all[] = {&w->level, &w->parent, &w->pedge, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->grow, &w->gent,
+    DBuf *all[] = {&w->level, &w->parent, &w->pedge, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->twid, &w->gent,
                    &w->diag, &w->tiles, &w->ptile, &w->U0, &w->U1, &w->h, &w->g0, &w->g1, &w->l0, &w->l1, &w->z,
                    &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1};
     for (DBuf *b : all) dfree(c, *b);
@@ -128,7 +128,7 @@ static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int f
     A(level, 4 * nv); A(parent, 4 * nv); A(pedge, 4 * nv); A(order, 4 * nv); A(pos, 4 * nv); A(key, 8 * nv);
     A(lvl_off, 4 * (nv + 2)); A(meta, 16);
     // padded so 16-byte aligned bulk copies of any row window stay inside the buffers
-    A(grow, 4 * (nv + 9)); A(gent, (nnz + 4) * (fp64 ? 16 : 8)); A(diag, es * (nv + 4));
+    A(gent, (nnz + 4) * (fp64 ? 16 : 8)); A(diag, es * (nv + 4));   // gent grows to the padded blocks
     A(ptile, 4 * (nv + 8));
     A(U0, xs * (nv + 1)); A(U1, xs * (nv + 1));   // + the zero slot
     A(h, es * 3 * nf);

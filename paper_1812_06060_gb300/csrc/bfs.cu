@@ -226,34 +226,80 @@ __global__ void k_row_len(const int32_t *__restrict__ order, int n, const int32_
     }
 }
 
-// row r of the level-ordered layout: neighbours renumbered to queue positions
-// with weight t*theta; idiag = 1 / (A_v + t * sum theta) (FP64, then rounded).
-// A neighbour without a queue position would mean inconsistent breadth-first
-// sets: it is pointed at the zero slot and the status word reports it.
-template <class T>
-__global__ void k_fill_layout(const int32_t *__restrict__ order, int n, const int32_t *__restrict__ rowptr,
-                              const int32_t *__restrict__ col, const int32_t *__restrict__ col_edge,
-                              const double *__restrict__ theta, const double *__restrict__ Av,
-                              const int32_t *__restrict__ pos, const int32_t *__restrict__ grow, double t,
-                              Ent<T> *gent, T *diag, int *status) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    int v = order[r];
-    int b = rowptr[v], e = rowptr[v + 1], o = grow[r];
-    double sum = 0.0;
-    for (int j = b; j < e; ++j) {
-        double th = theta[col_edge[j]];
-        sum += th;
-        Ent<T> x;
-        x.col = pos[col[j]];
-        if (x.col < 0) {   // a neighbour of a reached vertex is always reached
-            atomicCAS(status, DEV_OK, DEV_EINTERNAL);
-            x.col = n;     // the zero slot
-        }
-        x.w = (T)(t * th);
-        gent[o + (j - b)] = x;
+// Level-ordered operator, one block per tile in column-major ("ELL") order:
+// entry a of the row at tile position p (queue position start + p) sits at
+// gent[eb + a * cp + p], cp = count rounded up to 32, for a < W (the tile's
+// longest row); the entries of a row are its neighbours in ascending order,
+// renumbered to queue positions, with weight t*theta, and (zero slot n, 0)
+// past the row's end and in the padding columns.  A warp reading entry a of
+// 32 consecutive rows touches 32 consecutive entries.  idiag = 1 / (A_v +
+// t * sum theta) (FP64, then rounded).  A neighbour without a queue position
+// would mean inconsistent breadth-first sets: it is pointed at the zero slot
+// and the status word reports it.
+
+// widest row of each tile (one warp per tile); wsize[t] = W * cp
+__global__ void k_tile_width(const int32_t *__restrict__ ptile, int n_even, int n_odd, int tiles_cap,
+                             const int32_t *__restrict__ len, TileDesc *tiles, int32_t *wsize) {
+    const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (t >= tiles_cap) return;
+    const int ntiles = ptile[n_even] + ptile[n_even + 1 + n_odd];
+    if (t >= ntiles) {
+        if (lane == 0) wsize[t] = 0;
+        return;
     }
-    diag[r] = (T)(1.0 / (Av[v] + t * sum));
+    const int start = tiles[t].start, count = tiles[t].count;
+    int w = 0;
+    for (int p = lane; p < count; p += 32) w = max(w, len[start + p]);
+    for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if (lane == 0) {
+        tiles[t].ee = w;
+        wsize[t] = w * ((count + 31) & ~31);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TILE) k_fill_ell(const int32_t *__restrict__ ptile, int n_even, int n_odd,
+                                                  const int32_t *__restrict__ order, int n,
+                                                  const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                  const int32_t *__restrict__ col_edge,
+                                                  const double *__restrict__ theta, const double *__restrict__ Av,
+                                                  const int32_t *__restrict__ pos, const int32_t *__restrict__ eoff,
+                                                  double t, TileDesc *tiles, Ent<T> *gent, T *diag, int *status) {
+    const int ti = blockIdx.x;
+    const int ntiles = ptile[n_even] + ptile[n_even + 1 + n_odd];
+    if (ti >= ntiles) return;
+    const int start = tiles[ti].start, count = tiles[ti].count, W = tiles[ti].ee;
+    const int cp = (count + 31) & ~31;
+    const int64_t base = eoff[ti];
+    const int p = threadIdx.x;
+    if (p == 0) tiles[ti].eb = (int)base;
+    if (p >= cp) return;
+    int a = 0;
+    if (p < count) {
+        const int r = start + p;
+        const int v = order[r];
+        const int b = rowptr[v], e = rowptr[v + 1];
+        double sum = 0.0;
+        for (int j = b; j < e; ++j, ++a) {
+            const double th = theta[col_edge[j]];
+            sum += th;
+            Ent<T> x;
+            x.col = pos[col[j]];
+            if (x.col < 0) {   // a neighbour of a reached vertex is always reached
+                atomicCAS(status, DEV_OK, DEV_EINTERNAL);
+                x.col = n;     // the zero slot
+            }
+            x.w = (T)(t * th);
+            gent[base + (int64_t)a * cp + p] = x;
+        }
+        diag[r] = (T)(1.0 / (Av[v] + t * sum));
+    }
+    for (; a < W; ++a) {
+        Ent<T> z;
+        z.col = n;
+        z.w = T(0);
+        gent[base + (int64_t)a * cp + p] = z;
+    }
 }
 
 // tiles of at most TILE queue positions inside one set, listed set by set,
@@ -263,8 +309,8 @@ __device__ __forceinline__ int ntiles_of(const int32_t *lvl_off, int nlev, int i
     return (i < 0 || i >= nlev) ? 0 : (lvl_off[i + 1] - lvl_off[i] + TILE - 1) / TILE;
 }
 
-__global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_off, int nlev,
-                                              const int32_t *__restrict__ grow, int32_t *ptile, TileDesc *tiles) {
+__global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_off, int nlev, int32_t *ptile,
+                                              TileDesc *tiles) {
     int n_even = (nlev + 1) / 2, n_odd = nlev / 2;
     int32_t *p0 = ptile, *p1 = ptile + n_even + 1;
     for (int par = 0; par < 2; ++par) {
@@ -294,8 +340,7 @@ __global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_of
             d.start = s + k * TILE;
             d.count = min(TILE, e - d.start);
             d.lo = s;
-            d.eb = grow[d.start];
-            d.ee = grow[d.start + d.count];
+            d.eb = d.ee = 0;   // entry block and width: k_tile_width, k_fill_ell
             d.nt_prev = ntp;
             d.nt_self = nts;
             d.nt_next = ntn;
@@ -367,23 +412,32 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
     k_pos<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(q.pos)); ++c->launches;
     int32_t *len = ptr<int32_t>(q.n0);
     k_row_len<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), len); ++c->launches;
-    gh_status s = exclusive_scan_u32_dev(c, len, ptr<int32_t>(q.grow), n);
+    const size_t tiles_cap = (size_t)n / TILE + (size_t)q.nlev + 2;
+    gh_status s = dalloc(c, q.tiles, sizeof(TileDesc) * tiles_cap);
     if (s != GH_OK) return s;
+    if ((s = dalloc(c, q.twid, sizeof(int32_t) * (2 * tiles_cap + 2))) != GH_OK) return s;
+    k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.ptile), ptr<TileDesc>(q.tiles)); ++c->launches;
+    const int n_even = (q.nlev + 1) / 2, n_odd = q.nlev / 2;
+    int32_t *wsize = ptr<int32_t>(q.twid), *eoff = wsize + tiles_cap + 1;
+    k_tile_width<<<blocks_for((int64_t)tiles_cap * 32, 256), 256, 0, st>>>(ptr<int32_t>(q.ptile), n_even, n_odd,
+                                                                       (int)tiles_cap, len, ptr<TileDesc>(q.tiles),
+                                                                       wsize); ++c->launches;
+    GH_CUDA(cudaGetLastError());
+    int32_t total = 0;
+    if ((s = exclusive_scan_i32(c, wsize, eoff, (int64_t)tiles_cap, &total)) != GH_OK) return s;
+    const size_t es = q.fp64 ? sizeof(Ent<double>) : sizeof(Ent<float>);
+    if ((s = dalloc(c, q.gent, es * ((size_t)total + 4))) != GH_OK) return s;
     if (q.fp64) {
-        k_fill_layout<double><<<blocks_for(n, 256), 256, 0, st>>>(
-            ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
-            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t,
-            ptr<Ent<double>>(q.gent), ptr<double>(q.diag), c->status_dev); ++c->launches;
+        k_fill_ell<double><<<(unsigned)tiles_cap, TILE, 0, st>>>(
+            ptr<int32_t>(q.ptile), n_even, n_odd, ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
+            ptr<int32_t>(m.col_edge), ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), eoff, t,
+            ptr<TileDesc>(q.tiles), ptr<Ent<double>>(q.gent), ptr<double>(q.diag), c->status_dev); ++c->launches;
     } else {
-        k_fill_layout<float><<<blocks_for(n, 256), 256, 0, st>>>(
-            ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge),
-            ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), ptr<int32_t>(q.grow), t,
-            ptr<Ent<float>>(q.gent), ptr<float>(q.diag), c->status_dev); ++c->launches;
+        k_fill_ell<float><<<(unsigned)tiles_cap, TILE, 0, st>>>(
+            ptr<int32_t>(q.ptile), n_even, n_odd, ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
+            ptr<int32_t>(m.col_edge), ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), eoff, t,
+            ptr<TileDesc>(q.tiles), ptr<Ent<float>>(q.gent), ptr<float>(q.diag), c->status_dev); ++c->launches;
     }
-    s = dalloc(c, q.tiles, sizeof(TileDesc) * ((size_t)n / TILE + (size_t)q.nlev + 2));
-    if (s != GH_OK) return s;
-    k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.grow), ptr<int32_t>(q.ptile),
-                              ptr<TileDesc>(q.tiles)); ++c->launches;
     GH_CUDA(cudaGetLastError());
     q.t = t;
     return GH_OK;

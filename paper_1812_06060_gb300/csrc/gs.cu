@@ -32,7 +32,10 @@
 //
 // Vertices sit in breadth-first queue order, so D_i is a contiguous range and
 // the set of a neighbour follows from its position alone.  A tile is TILE
-// consecutive positions inside one set.
+// consecutive positions inside one set; its rows are one column-major block
+// (entry a of position p at a * cp + p, padded with zero-weight entries to the
+// tile's longest row), so the 32 lanes of a warp reading entry a of their
+// rows read 32 consecutive entries of shared memory.
 //
 // Each heat value is carried as (mantissa, binary exponent): the solution
 // falls by about e^-1 per edge length and leaves the FP32 (and FP64) range a
@@ -60,7 +63,6 @@ template <class T> struct GsJob {
     int ntickets;          // tiles over all steps
     int zero_pos;          // a position that always holds the zero state (nreach)
     const int32_t *lvl_off;
-    const int32_t *grow;
     const Ent<T> *gent;
     const T *diag;
     const int32_t *ptile0;
@@ -237,21 +239,19 @@ __device__ bool wait_sets(const int32_t *p0, int t0, const int32_t *p1, int t1, 
 constexpr int kCW = 8;                        // consumer warps per CTA
 constexpr int kThreads = 32 * (kCW + 1);      // + one producer warp
 constexpr int kVPT = TILE / (32 * kCW);       // positions per consumer thread
-constexpr int kEntPerV = 7;                   // staged entries per position (longer tiles read from global)
+constexpr int kEntStage = kMaxDeg * TILE;     // staged row entries (wider tiles read their rows from global)
 static_assert(kVPT * 32 * kCW == TILE, "tile must split evenly over the consumer threads");
 
 // one staging buffer: the tile's row pointers, diagonal and rows, plus the
 // tile's facts written by the producer
 template <class T> struct alignas(128) Stage {
-    Ent<T> ent[TILE * kEntPerV + 4];
-    int grow[TILE + 12];
+    Ent<T> ent[kEntStage];
     T diag[TILE + 8];
-    int start, count, lo, k, level, g0, d0, e0, fits, abort, finished, q;
+    int start, count, lo, k, level, cp, w, d0, e0, fits, abort, finished, q, pad[3];
 };
 // every bulk-copy destination must start on a 16-byte boundary, in both stages
 static_assert(sizeof(Stage<float>) % 16 == 0 && sizeof(Stage<double>) % 16 == 0, "stage size");
-static_assert(offsetof(Stage<float>, grow) % 16 == 0 && offsetof(Stage<float>, diag) % 16 == 0, "stage layout");
-static_assert(offsetof(Stage<double>, grow) % 16 == 0 && offsetof(Stage<double>, diag) % 16 == 0, "stage layout");
+static_assert(offsetof(Stage<float>, diag) % 16 == 0 && offsetof(Stage<double>, diag) % 16 == 0, "stage layout");
 
 constexpr int kMaxJobs = 256;                 // queries per launch (larger batches take several launches)
 
@@ -312,7 +312,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         // Producer warp.  Lane l looks up the l-th of the next 32 candidates
         // (one parallel lookup per 32); lane 0 then stages, waits and releases
         // the valid ones one by one.
-        constexpr int EA = 16 / (int)sizeof(Ent<T>);   // entries per 16 bytes
         constexpr int DA = 16 / (int)sizeof(T);        // diagonal values per 16 bytes
         uint32_t eph[2] = {0u, 0u};
         int j = 0;
@@ -371,19 +370,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                         eph[b] ^= 1u;
                     }
                     if (ok) {
-                        const int g0 = d.start & ~3, g1 = (d.start + d.count + 1 + 3) & ~3;
+                        // the tile's row block (cp * W entries from a multiple of 32) and diagonal
+                        const int cp = (d.count + 31) & ~31, nent = cp * d.ee;
                         const int d0 = d.start & ~(DA - 1), d1 = (d.start + d.count + DA - 1) & ~(DA - 1);
-                        const int e0 = d.eb & ~(EA - 1), e1 = (d.ee + EA - 1) & ~(EA - 1);
-                        const int fits = (e1 - e0) <= TILE * kEntPerV + 4;
-                        const uint32_t bg = 4u * (g1 - g0), bd = (uint32_t)sizeof(T) * (d1 - d0);
-                        const uint32_t be = fits ? (uint32_t)sizeof(Ent<T>) * (e1 - e0) : 0u;
+                        const int fits = nent <= kEntStage;
+                        const uint32_t bd = (uint32_t)sizeof(T) * (d1 - d0);
+                        const uint32_t be = fits ? (uint32_t)sizeof(Ent<T>) * nent : 0u;
                         fence_proxy_async();
-                        mbar_expect_tx_only(&full[b], bg + bd + be);
-                        bulk_g2s(S.grow, J.grow + g0, bg, &full[b]);
+                        mbar_expect_tx_only(&full[b], bd + be);
                         bulk_g2s(S.diag, J.diag + d0, bd, &full[b]);
-                        if (be) bulk_g2s(S.ent, J.gent + e0, be, &full[b]);
+                        if (be) bulk_g2s(S.ent, J.gent + d.eb, be, &full[b]);
                         S.start = d.start; S.count = d.count; S.lo = d.lo; S.k = k; S.level = i;
-                        S.g0 = g0; S.d0 = d0; S.e0 = e0; S.fits = fits; S.q = q;
+                        S.cp = cp; S.w = d.ee; S.d0 = d0; S.e0 = d.eb; S.fits = fits; S.q = q;
                         if (pv0 >= t0 && pv1 >= t1 && pv2 >= t2)
                             fence_acquire();
                         else
@@ -418,28 +416,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         fph[b] ^= 1u;
         if (S.abort) return;
         const int start = S.start, count = S.count, lo = S.lo, k = S.k, level = S.level;
-        const int sg = S.g0, sd = S.d0, se = S.e0;
+        const int cp = S.cp, wt = S.w, sd = S.d0;
         const bool fits = S.fits != 0;
         const GsJob<T> &J = jobs[S.q];
         XVal<T> *Ucur = J.U[k & 1];
         const XVal<T> *Uprv = J.U[(k & 1) ^ 1];
-        int rb[kVPT], re[kVPT];
+        const Ent<T> *E = fits ? S.ent : J.gent + S.e0;   // the tile's row block
         XVal<T> u[kVPT][kMaxDeg];
 #pragma unroll
         for (int v = 0; v < kVPT; ++v) {
             const int p = v * 32 * kCW + cw * 32 + lane;
-            rb[v] = re[v] = 0;
-            if (p < count) {
-                const int r = start + p;
-                rb[v] = S.grow[r - sg] - se;
-                re[v] = S.grow[r - sg + 1] - se;
-            }
-            // all gathers of the thread go out together; a missing entry reads
-            // the zero state kept at position nreach
+            // all gathers of the thread go out together; entries past the
+            // block's width read the zero state kept at position nreach
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) {
                 int c = J.zero_pos;
-                if (rb[v] + a < re[v]) c = fits ? S.ent[rb[v] + a].col : J.gent[se + rb[v] + a].col;
+                if (p < count && a < wt) c = E[a * cp + p].col;
                 u[v][a] = ld_state((c < lo ? Ucur : Uprv) + c);
             }
         }
@@ -452,20 +444,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
             int eref = (lo == 0) ? 1 : kZeroExp;   // zero states carry kZeroExp: no test needed
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) eref = max(eref, u[v][a].e);
-            for (int a = rb[v] + kMaxDeg; a < re[v]; ++a) {  // long rows
-                const Ent<T> x = fits ? S.ent[a] : J.gent[se + a];
+            for (int a = kMaxDeg; a < wt; ++a) {  // rows longer than kMaxDeg
+                const Ent<T> x = E[a * cp + p];
                 const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
                 if (w.m != T(0)) eref = max(eref, w.e);
             }
             T acc = (lo == 0) ? xscale(T(0.5), 1 - eref) : T(0);
 #pragma unroll
             for (int a = 0; a < kMaxDeg; ++a) {
-                T w = T(0);
-                if (rb[v] + a < re[v]) w = fits ? S.ent[rb[v] + a].w : J.gent[se + rb[v] + a].w;
+                const T w = (a < wt) ? E[a * cp + p].w : T(0);
                 acc += w * xscale(u[v][a].m, u[v][a].e - eref);
             }
-            for (int a = rb[v] + kMaxDeg; a < re[v]; ++a) {
-                const Ent<T> x = fits ? S.ent[a] : J.gent[se + a];
+            for (int a = kMaxDeg; a < wt; ++a) {
+                const Ent<T> x = E[a * cp + p];
                 const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
                 acc += x.w * xscale(w.m, w.e - eref);
             }
@@ -535,7 +526,6 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
         j.nsteps = w.nlev + 2 * (sweeps - 1);
         j.n_even = (w.nlev + 1) / 2;
         j.lvl_off = ptr<int32_t>(w.lvl_off);
-        j.grow = ptr<int32_t>(w.grow);
         j.gent = ptr<Ent<T>>(w.gent);
         j.diag = ptr<T>(w.diag);
         j.ptile0 = ptr<int32_t>(w.ptile);

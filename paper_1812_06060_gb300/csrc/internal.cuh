@@ -73,7 +73,7 @@ template <class T> struct alignas(sizeof(T) == 4 ? 8 : 16) Ent {
 // One Gauss-Seidel tile: up to TILE consecutive queue positions of one set.
 struct alignas(16) TileDesc {
     int level, start, count, lo;      // set index, first position, positions, first position of the set
-    int eb, ee, nt_prev, nt_self;     // entry range [eb, ee) of its rows; tiles in sets i-1 and i
+    int eb, ee, nt_prev, nt_self;     // first entry of its row block, width W; tiles in sets i-1 and i
     int nt_next, pad0, pad1, pad2;    // tiles in set i+1 (0 past the last set)
 };
 
@@ -152,8 +152,8 @@ struct QueryWs {
     DBuf level, parent, order, pos, key, lvl_off, meta;  // meta: [0] nlev [1] nreach [2] err
     DBuf pedge;     // int32 [nv] edge from each vertex to its pairing vertex
     // level-ordered Gauss-Seidel layout
-    DBuf grow;      // int32 [nv+1] (+ padding for aligned bulk copies)
-    DBuf gent;      // Ent<T> [2ne] (+ padding)
+    DBuf gent;      // Ent<T>: one column-major block per tile (see k_fill_ell)
+    DBuf twid;      // int32 [2 tiles + 2]: block size and offset of each tile
     DBuf diag;      // T [nv] (+ padding): 1 / (A_v + t sum theta)
     DBuf tiles;     // TileDesc [nreach/TILE + nlev], sorted by (parity, level)
     DBuf ptile;     // int32 [nv + 8] per-parity tile prefix over levels

@@ -401,8 +401,11 @@ __global__ void k_jump(int64_t nv, const double *__restrict__ d_in, const int32_
 
 // per reached vertex r (queue order): (A - t L_c) u - u_0 in FP64
 template <class T>
-__global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restrict__ grow, const Ent<T> *__restrict__ gent,
-                                                   const T *__restrict__ diag,
+__global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restrict__ order,
+                                                   const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                   const int32_t *__restrict__ col_edge,
+                                                   const double *__restrict__ theta, const int32_t *__restrict__ pos,
+                                                   double t, const T *__restrict__ diag,
                                                    const int32_t *__restrict__ lvl_off, const XVal<T> *__restrict__ U,
                                                    double *part) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,10 +414,13 @@ __global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restr
         XVal<T> ur = U[r];
         double uv = ldexp((double)ur.m, max(ur.e, -2000));
         double res = uv / (double)diag[r];   // diag holds 1 / (A_v + t sum theta)
-        for (int a = grow[r]; a < grow[r + 1]; ++a) {
-            Ent<T> en = gent[a];
-            XVal<T> uc = U[en.col];
-            res -= (double)en.w * ldexp((double)uc.m, max(uc.e, -2000));
+        const int v = order[r];
+        for (int j = rowptr[v]; j < rowptr[v + 1]; ++j) {
+            const int c = pos[col[j]];
+            if (c < 0) continue;
+            const T w = (T)(t * theta[col_edge[j]]);   // the weight the sweeps use
+            XVal<T> uc = U[c];
+            res -= (double)w * ldexp((double)uc.m, max(uc.e, -2000));
         }
         if (r < lvl_off[1]) res -= 1.0;
         acc = res * res;
@@ -524,14 +530,16 @@ template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, d
     return GH_OK;
 }
 
-template <class T> gh_status heat_resid_t(Ctx *c, QueryWs &q) {
+template <class T> gh_status heat_resid_t(Ctx *c, const DevMesh &m, QueryWs &q) {
     cudaStream_t st = c->stream;
     int n = q.nreach;
     unsigned nb = blocks_for(n, NT);
     double *part = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
-    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.grow), ptr<Ent<T>>(q.gent), ptr<T>(q.diag), ptr<int32_t>(q.lvl_off),
-                                       ptr<XVal<T>>(q.final_buf ? q.U1 : q.U0), part); ++c->launches;
+    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.order), ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
+                                       ptr<int32_t>(m.col_edge), ptr<double>(m.theta), ptr<int32_t>(q.pos), q.t,
+                                       ptr<T>(q.diag), ptr<int32_t>(q.lvl_off), ptr<XVal<T>>(q.final_buf ? q.U1 : q.U0),
+                                       part); ++c->launches;
     double *tmp = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * 2, st));
     k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, tmp); ++c->launches;
@@ -566,8 +574,7 @@ gh_status run_integrate(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out_dev)
     return q.fp64 ? integrate_t<double>(c, m, q, d_out_dev) : integrate_t<float>(c, m, q, d_out_dev);
 }
 gh_status run_heat_residual(Ctx *c, const DevMesh &m, QueryWs &q) {
-    (void)m;
-    return q.fp64 ? heat_resid_t<double>(c, q) : heat_resid_t<float>(c, q);
+    return q.fp64 ? heat_resid_t<double>(c, m, q) : heat_resid_t<float>(c, m, q);
 }
 
 }  // namespace gh
