@@ -139,6 +139,20 @@ gh_status gh_mesh_load(gh_ctx ctx, const double *V, int64_t nv, const int32_t *F
  * pointer may be NULL. */
 gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, double *mean_edge_len);
 
+/* Launch shape of the breadth-first traversal (Sec. 3.3): one thread-block
+ * cluster of `bfs_cluster` CTAs (8, or 16 where the device allows clusters
+ * that large) walks the sets of each query.  By default the size is tuned
+ * per mesh on the first solve of each kind ([0] a single query, [1] a
+ * batch): every supported size runs once, timed, and the fastest is kept.
+ * All sizes give the same sets, pairing and order.  The paper's traversal
+ * is sequential and has no counterpart.
+ * gh_mesh_tuning: writes the sizes in use (0: not tuned yet) to
+ *   bfs_cluster[2].
+ * gh_mesh_set_tuning: kind 0 or 1; size 0 (tune again), 8 or 16.
+ *   GH_EINVAL for another kind or size, or a size the device cannot place. */
+gh_status gh_mesh_tuning(gh_mesh mesh, int32_t *bfs_cluster);
+gh_status gh_mesh_set_tuning(gh_mesh mesh, int32_t kind, int32_t bfs_cluster);
+
 /* Frees the mesh; GH_EBUSY while serving requests on it are in flight. */
 gh_status gh_mesh_free(gh_mesh mesh);
 

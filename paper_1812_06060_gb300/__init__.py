@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: 
 # symbols declared in include/geoheat.h
 EXPORTS = ["gh_params_default", "gh_version", "gh_ctx_create", "gh_ctx_destroy", "gh_ctx_set_stream", "gh_ctx_set_wait_limit", "gh_ctx_memory",
            "gh_ctx_stats",
-           "gh_mesh_load", "gh_mesh_info", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
+           "gh_mesh_load", "gh_mesh_info", "gh_mesh_tuning", "gh_mesh_set_tuning", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
            "gh_debug_dump", "gh_stage_times", "gh_mean_edge_length_noalloc", "gh_serve_config", "gh_submit", "gh_poll",
            "gh_wait", "gh_last_error"]
 
@@ -84,6 +84,10 @@ def load_library(path: str = LIB_PATH):
     L.gh_mesh_load.argtypes = [P, P, I64, P, I64, C.POINTER(P)]
     L.gh_mesh_info.restype = S
     L.gh_mesh_info.argtypes = [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D)]
+    L.gh_mesh_tuning.restype = S
+    L.gh_mesh_tuning.argtypes = [P, C.POINTER(I32)]
+    L.gh_mesh_set_tuning.restype = S
+    L.gh_mesh_set_tuning.argtypes = [P, I32, I32]
     L.gh_mesh_free.restype = S
     L.gh_mesh_free.argtypes = [P]
     L.gh_solve.restype = S
@@ -234,6 +238,16 @@ class Mesh:
         src = np.ascontiguousarray(np.concatenate([np.asarray(s, np.int32) for s in source_sets]), dtype=np.int32)
         _check(lib().gh_solve_batch(self.handle, _addr(off), _addr(src), len(source_sets), C.byref(prm), _addr(out)))
         return out
+
+    def tuning(self) -> tuple:
+        """Breadth-first cluster sizes in use (single query, batch); 0 = not tuned yet."""
+        out = (C.c_int32 * 2)()
+        _check(lib().gh_mesh_tuning(self.handle, out))
+        return int(out[0]), int(out[1])
+
+    def set_tuning(self, kind: int, bfs_cluster: int):
+        """Force the breadth-first cluster size (8 or 16) for kind 0 (single) or 1 (batch); 0 tunes again."""
+        _check(lib().gh_mesh_set_tuning(self.handle, kind, bfs_cluster))
 
     def dump(self, what: int, query: int = 0) -> np.ndarray:
         n, eb = C.c_int64(), C.c_int32()

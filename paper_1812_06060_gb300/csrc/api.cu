@@ -430,6 +430,33 @@ gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, doub
     return GH_OK;
 }
 
+gh_status gh_mesh_tuning(gh_mesh mesh, int32_t *bfs_cluster) {
+    if (!mesh || !bfs_cluster) { set_error("NULL argument"); return GH_EINVAL; }
+    DevMesh &m = mesh->h.m;
+    std::lock_guard<std::mutex> lk(*m.rec_mu);
+    bfs_cluster[0] = m.bfs_cluster[0];
+    bfs_cluster[1] = m.bfs_cluster[1];
+    return GH_OK;
+}
+
+gh_status gh_mesh_set_tuning(gh_mesh mesh, int32_t kind, int32_t bfs_cluster) {
+    if (!mesh) { set_error("mesh is NULL"); return GH_EINVAL; }
+    if (kind != 0 && kind != 1) { set_error("kind must be 0 (single query) or 1 (batch)"); return GH_EINVAL; }
+    if (bfs_cluster != 0 && bfs_cluster != 8 && bfs_cluster != 16) {
+        set_error("bfs_cluster must be 0 (tune), 8 or 16");
+        return GH_EINVAL;
+    }
+    GH_CUDA(cudaSetDevice(mesh->ctx->c.device));
+    if (bfs_cluster != 0 && !bfs_cluster_supported(bfs_cluster)) {
+        set_error("this device cannot place clusters of " + std::to_string(bfs_cluster) + " CTAs");
+        return GH_EINVAL;
+    }
+    DevMesh &m = mesh->h.m;
+    std::lock_guard<std::mutex> lk(*m.rec_mu);
+    m.bfs_cluster[kind] = bfs_cluster;
+    return GH_OK;
+}
+
 gh_status gh_mesh_free(gh_mesh mesh) {
     if (!mesh) return GH_EINVAL;
     if (mesh->h.inflight.load() > 0) { set_error("mesh has serving requests in flight"); return GH_EBUSY; }

@@ -61,7 +61,6 @@ __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
     return total;
 }
 
-constexpr int kBfsCluster = 8;  // CTAs (one cluster) walking the sets of one query
 
 // Keys: a vertex discovered by the parent of queue rank r through the
 // parent's slot j holds ((r + 1) << 32 | j); sources hold 0 and undiscovered
@@ -69,8 +68,9 @@ constexpr int kBfsCluster = 8;  // CTAs (one cluster) walking the sets of one qu
 // vertex always holds a key below every key a later set offers, so the
 // offers need no "already visited" test.
 //
-// One cluster of kBfsCluster CTAs walks the sets of one query.  The parents
-// of a set (a contiguous range of queue ranks) are split into kBfsCluster
+// One cluster of CL CTAs (8, or 16 where the device allows clusters that
+// large) walks the sets of one query.  The parents of a set (a contiguous
+// range of queue ranks) are split into CL
 // contiguous shares, one per CTA, each taken in chunks of BT ranks (one rank
 // per thread).  Per set:
 //   offers: every thread offers its parents' keys to their neighbours
@@ -102,17 +102,17 @@ __device__ __forceinline__ int bfs_children(const BfsArgs &a, int r, int b, int 
     return k;
 }
 
-__global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
+template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *__restrict__ all) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
-    const BfsArgs a = all[blockIdx.x / kBfsCluster];
+    const BfsArgs a = all[blockIdx.x / CL];
     __shared__ int s_total;
     int lo = 0, hi = a.n0, nlev = 1;
     if (crank == 0 && threadIdx.x == 0) a.lvl_off[0] = 0;
     while (true) {
         const int n = hi - lo;
-        const int per = (n + kBfsCluster - 1) / kBfsCluster;
+        const int per = (n + CL - 1) / CL;
         const int mlo = min(hi, lo + crank * per), mhi = min(hi, mlo + per);
         const int nchunk = (mhi - mlo + BT - 1) / BT;
         // offers; the first chunk's row stays in registers
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(BT) k_bfs(const BfsArgs *__restrict__ all) {
         if (threadIdx.x == 0) s_total = mytotal;
         cluster.sync();
         int before = 0, total = 0;
-        for (int q = 0; q < kBfsCluster; ++q) {
+        for (int q = 0; q < CL; ++q) {
             const int t = *cluster.map_shared_rank(&s_total, q);
             if (q < crank) before += t;
             total += t;
@@ -352,7 +352,59 @@ __global__ void __launch_bounds__(BT) k_tiles(const int32_t *__restrict__ lvl_of
 
 }  // namespace
 
-gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src) {
+namespace {
+
+template <int CL> cudaError_t launch_bfs(const BfsArgs *dargs, int K, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K * CL);
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_bfs<CL>, dargs);
+}
+
+// can clusters of CL CTAs of BT threads be placed on this device at all?
+template <int CL> bool bfs_cluster_fits() {
+    if (CL > 8 && cudaFuncSetAttribute(k_bfs<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(BT);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_bfs<CL>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+}  // namespace
+
+bool bfs_cluster_supported(int cl) {
+    if (cl == 8) return bfs_cluster_fits<8>();
+    if (cl == 16) return bfs_cluster_fits<16>();
+    return false;
+}
+
+// One breadth-first launch for all queries, with clusters of `cl` CTAs.
+static gh_status run_bfs_once(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws,
+                              const std::vector<std::vector<int32_t>> &src, int cl) {
     cudaStream_t st = c->stream;
     int K = (int)src.size();
     std::vector<BfsArgs> args(K);
@@ -365,35 +417,18 @@ gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const st
         k_seed<<<blocks_for((int64_t)src[q].size(), 256), 256, 0, st>>>(ptr<int32_t>(w.level), ptr<unsigned long long>(w.key), ptr<int32_t>(w.order),
                                                                        (int)src[q].size()); ++c->launches;
         args[q] = BfsArgs{ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge), ptr<int32_t>(w.level),
-                          ptr<int32_t>(w.parent), ptr<int32_t>(w.pedge), ptr<int32_t>(w.order), ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off),
-                          ptr<int32_t>(w.meta), (int32_t)src[q].size()};
+                          ptr<int32_t>(w.parent), ptr<int32_t>(w.pedge), ptr<int32_t>(w.order),
+                          ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off), ptr<int32_t>(w.meta),
+                          (int32_t)src[q].size()};
     }
     BfsArgs *dargs = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&dargs, sizeof(BfsArgs) * K, st));
     GH_CUDA(cudaMemcpyAsync(dargs, args.data(), sizeof(BfsArgs) * K, cudaMemcpyHostToDevice, st));
-    {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(K * kBfsCluster);
-        cfg.blockDim = dim3(BT);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kBfsCluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t le0 = cudaLaunchKernelEx(&cfg, k_bfs, (const BfsArgs *)dargs);
-        ++c->launches;
-        if (le0 != cudaSuccess) {
-            cudaFreeAsync(dargs, st);
-            return cuda_fail(le0, "cluster launch of k_bfs");
-        }
-    }
-    cudaError_t le = cudaGetLastError();
+    cudaError_t le0 = (cl == 16) ? launch_bfs<16>(dargs, K, st) : launch_bfs<8>(dargs, K, st);
+    ++c->launches;
+    cudaError_t le = (le0 != cudaSuccess) ? le0 : cudaGetLastError();
     cudaFreeAsync(dargs, st);
-    if (le != cudaSuccess) return cuda_fail(le, "k_bfs");
+    if (le != cudaSuccess) return cuda_fail(le, "cluster launch of k_bfs");
     std::vector<int32_t> meta(2 * K);
     for (int q = 0; q < K; ++q)
         GH_CUDA(cudaMemcpyAsync(&meta[2 * q], ws[q]->meta.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -402,6 +437,44 @@ gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const st
         ws[q]->nlev = meta[2 * q];
         ws[q]->nreach = meta[2 * q + 1];
     }
+    return GH_OK;
+}
+
+// The breadth-first sets of every query.  The cluster size is tuned per mesh,
+// separately for single queries and batches: the first solve of each kind
+// runs every size the device supports once, timed with events, and keeps
+// the fastest (all sizes give the same sets and order, so the last run's
+// result is the solve's).
+gh_status run_bfs(Ctx *c, DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src) {
+    const int kind = src.size() > 1 ? 1 : 0;
+    int cl;
+    {
+        std::lock_guard<std::mutex> lk(*m.rec_mu);
+        cl = m.bfs_cluster[kind];
+    }
+    if (cl != 0) return run_bfs_once(c, m, ws, src, cl);
+    std::vector<int> cand = {8};
+    if (bfs_cluster_supported(16)) cand.push_back(16);
+    cudaEvent_t e0, e1;
+    GH_CUDA(cudaEventCreate(&e0));
+    GH_CUDA(cudaEventCreate(&e1));
+    float best_ms = 0.0f;
+    int best = 8;
+    gh_status s = GH_OK;
+    for (int x : cand) {
+        cudaEventRecord(e0, c->stream);
+        if ((s = run_bfs_once(c, m, ws, src, x)) != GH_OK) break;   // synchronises the stream
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (x == cand[0] || ms < best_ms) { best_ms = ms; best = x; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != GH_OK) return s;
+    std::lock_guard<std::mutex> lk(*m.rec_mu);
+    if (m.bfs_cluster[kind] == 0) m.bfs_cluster[kind] = best;
     return GH_OK;
 }
 

@@ -141,7 +141,10 @@ struct DevMesh {
     // twin weight A'/(A + A'), then sqrt(A_f): 16 values (FP32 and FP64
     // copies), built on the first face-form solve
     DBuf face_rec32, face_rec64;
-    std::shared_ptr<std::mutex> rec_mu = std::make_shared<std::mutex>();
+    // breadth-first cluster size per kind of solve ([0] one query, [1] a
+    // batch): 0 until tuned on the first solve of that kind, or set by the user
+    int bfs_cluster[2] = {0, 0};
+    std::shared_ptr<std::mutex> rec_mu = std::make_shared<std::mutex>();   // guards the lazily built parts
 };
 
 // Per-query workspace (BFS products, the level-ordered layout, solver state).
@@ -207,7 +210,8 @@ gh_status exclusive_scan_u32_dev(Ctx *c, const int32_t *in, int32_t *out, int64_
 gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_dev);
 
 // bfs.cu
-gh_status run_bfs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src);
+gh_status run_bfs(Ctx *c, DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src);
+bool bfs_cluster_supported(int cl);
 gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
 
 // gs.cu

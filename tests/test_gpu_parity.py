@@ -186,12 +186,22 @@ def _chunks_per_cta(level):
     return ((widest + 7) // 8 + 1023) // 1024
 
 
+def _force_cluster(gh, M, kind, cl):
+    try:
+        M.set_tuning(kind, cl)
+    except gh.GeoheatError as e:
+        assert e.status == gh.GH_EINVAL
+        pytest.skip(f"clusters of {cl} CTAs cannot be placed on this device")
+
+
+@pytest.mark.parametrize("cl", [8, 16])
 @pytest.mark.parametrize("nx,step", [(5000, 2), (10000, 2), (17000, 2), (50000, 2), (3000, 1)])
-def test_wide_sets_bfs_exact(gh, ctx, nx, step):
+def test_wide_sets_bfs_exact(gh, ctx, nx, step, cl):
     """Breadth-first sets far wider than one block of the cluster: every CTA
     takes its share of a set in several chunks (up to 10 here).  step 1 puts
     adjacent vertices in the source set, so a source is the first neighbour
-    of the lowest-ranked source.  Sets, pairing, queue order: bit-exact."""
+    of the lowest-ranked source.  Sets, pairing, queue order: bit-exact, with
+    clusters of 8 and of 16 CTAs."""
     mesh = meshgen.strip_grid(nx, 6)
     src = np.arange(0, nx, step, dtype=np.int32)
     md = oracle.mesh_data(mesh.V, mesh.F)
@@ -200,8 +210,10 @@ def test_wide_sets_bfs_exact(gh, ctx, nx, step):
         assert _chunks_per_cta(ref.level) == {5000: 1, 10000: 2, 17000: 4, 50000: 10}[nx]
     M = gh.Mesh(ctx, mesh.V, mesh.F)
     try:
+        _force_cluster(gh, M, 0, cl)
         out = np.empty(md.nv)
         M.solve(src, out, gh.params(gs_sweeps=2, admm_iters=1, form="edge"))
+        assert M.tuning()[0] == cl
         assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL), ref.level)
         assert np.array_equal(M.dump(gh.GH_DUMP_PARENT), ref.parent)
         assert np.array_equal(M.dump(gh.GH_DUMP_ORDER), ref.order)
@@ -213,7 +225,8 @@ def test_wide_sets_bfs_exact(gh, ctx, nx, step):
 
 def test_wide_sets_batch(gh, ctx):
     """Several wide-front queries in one batch (one cluster each): each
-    query's sets and order equal the oracle's."""
+    query's sets and order equal the oracle's.  The batch's cluster size is
+    tuned on this first batch solve and must be one the device supports."""
     nx = 17000
     mesh = meshgen.strip_grid(nx, 5)
     md = oracle.mesh_data(mesh.V, mesh.F)
@@ -222,7 +235,9 @@ def test_wide_sets_batch(gh, ctx):
     M = gh.Mesh(ctx, mesh.V, mesh.F)
     try:
         out = np.empty((len(sets), md.nv))
+        assert M.tuning() == (0, 0)
         M.solve_batch(sets, out, gh.params(gs_sweeps=2, admm_iters=1, form="face"))
+        assert M.tuning()[0] == 0 and M.tuning()[1] in (8, 16)
         for q, s_ in enumerate(sets):
             ref = oracle.bfs(md, s_)
             assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL, q), ref.level), q
@@ -293,6 +308,10 @@ def test_errors(gh, ctx):
     with pytest.raises(gh.GeoheatError) as e:
         M.solve(np.array([0], np.int32), d, gh.params(gs_sweeps=0))
     assert e.value.status == gh.GH_EINVAL
+    for kind, cl in ((0, 7), (2, 8), (-1, 16), (1, 32)):
+        with pytest.raises(gh.GeoheatError) as e:
+            M.set_tuning(kind, cl)
+        assert e.value.status == gh.GH_EINVAL
     M.close()
     V = np.zeros((5, 3))
     V[:, 0] = [0, 1, 0, 0, 1]
