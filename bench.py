@@ -544,6 +544,7 @@ def run_workload(args):
         M.solve(w.sources[1], one, prm)
         single_s = time.perf_counter() - t0
         st1 = M.stage_times()
+        nlev1 = len(M.dump(g.GH_DUMP_LEVEL_OFF, 0)) - 1
         K = len(w.sources)
         dout = torch.empty((K, w.mesh.nv), dtype=torch.float64, device="cuda")
         t0 = time.perf_counter()
@@ -559,7 +560,6 @@ def run_workload(args):
                     "gs_algorithmic_GBps_batch": K * gs_bytes(V, M.ne, sweeps) / (stb[5] / 1000.0) / 1e9,
                     "device_bytes": ctx.memory()})
         peak, _ = measured_peaks()
-        nlev1 = len(M.dump(g.GH_DUMP_LEVEL_OFF, K - 1)) - 1
         sb = stage_bytes(V, M.ne, w.mesh.nf, sweeps, 10, form, nlev1)
         out["stage_roofline_single"] = stage_roofline(st1, sb, peak)
         out["stage_roofline_batch"] = stage_roofline(stb, {k: K * v for k, v in sb.items()}, peak)

@@ -12,6 +12,7 @@
 namespace gh {
 struct Engine;
 void engine_stop(Engine *e);
+void engine_forget_mesh(Engine *e, DevMesh *m);
 }
 
 struct gh_ctx_s {
@@ -162,12 +163,78 @@ size_t ws_bytes(const DevMesh &m, int fp64, int form) {
     return b + (1 << 20);
 }
 
-// Run queries src[0..K) through the whole path; d_out (device) gets K x nv.
+// The whole path for a list of queries, each with its own mesh, workspace,
+// sources, parameters and (device) output; all of one precision.  One
+// breadth-first launch and one diffusion launch serve every query; the other
+// stages run per query.  stage_ms6 (may be null) gets the stage times.
+gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
+    const int K = (int)items.size();
+    gh_status s = GH_OK;
+    for (Item &it : items) {
+        if ((s = ensure_ws(c, *it.m, *it.w, it.p->fp64, it.p->form, it.p->admm_iters)) != GH_OK) return s;
+        it.w->diagnostics = it.p->diagnostics;
+        it.w->sweeps = it.p->gs_sweeps;
+    }
+    std::vector<DevMesh *> meshes(K);
+    std::vector<QueryWs *> ws(K);
+    std::vector<std::vector<int32_t>> srcs(K);
+    for (int q = 0; q < K; ++q) {
+        meshes[q] = items[q].m;
+        ws[q] = items[q].w;
+        srcs[q] = *items[q].src;
+    }
+    cudaEvent_t ev[8];
+    for (auto &e : ev) GH_CUDA(cudaEventCreate(&e));
+    do {
+        cudaEventRecord(ev[0], c->stream);
+        if ((s = run_bfs(c, meshes, ws, srcs)) != GH_OK) break;
+        for (int q = 0; q < K && s == GH_OK; ++q) {
+            const gh_params *p = items[q].p;
+            const double t = (p->t > 0) ? p->t : p->m * items[q].m->hbar * items[q].m->hbar;
+            s = build_layout(c, *items[q].m, *ws[q], t);
+        }
+        if (s != GH_OK) break;
+        cudaEventRecord(ev[1], c->stream);
+        if ((s = run_gs(c, ws, ev[6], ev[7])) != GH_OK) break;
+        cudaEventRecord(ev[2], c->stream);
+        // no host synchronisation here: a diffusion timeout leaves every index
+        // in range, and the status word is read once the solve is done
+        for (int q = 0; q < K && s == GH_OK; ++q) {
+            if (items[q].p->diagnostics) s = run_heat_residual(c, *items[q].m, *ws[q]);
+            if (s == GH_OK) s = run_normalize(c, *items[q].m, *ws[q]);
+        }
+        cudaEventRecord(ev[3], c->stream);
+        for (int q = 0; q < K && s == GH_OK; ++q) {
+            const gh_params *p = items[q].p;
+            s = (p->form == GH_FORM_FACE) ? run_face_admm(c, *items[q].m, *ws[q], p->admm_iters, p->mu)
+                                          : run_edge_admm(c, *items[q].m, *ws[q], p->admm_iters, p->mu);
+        }
+        cudaEventRecord(ev[4], c->stream);
+        for (int q = 0; q < K && s == GH_OK; ++q) s = run_integrate(c, *items[q].m, *ws[q], items[q].d_out_dev);
+        cudaEventRecord(ev[5], c->stream);
+        if (s != GH_OK) break;
+        if ((s = check_status(c, "solve")) != GH_OK) break;
+        if (stage_ms6) {
+            for (int i = 0; i < 5; ++i) {
+                float x = 0;
+                cudaEventElapsedTime(&x, ev[i], ev[i + 1]);
+                stage_ms6[i] += x;
+            }
+            float xg = 0;
+            cudaEventElapsedTime(&xg, ev[6], ev[7]);
+            stage_ms6[5] += xg;
+        }
+    } while (false);
+    for (auto &e : ev) cudaEventDestroy(e);
+    return s;
+}
+
+// Run queries src[0..K) of one mesh through the whole path; d_out (device)
+// gets K x nv.  Queries go in passes of as many as the budget (or 80% of
+// free memory) allows, at most 64.
 gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
                      const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k) {
     const int K = (int)src.size();
-    const double t = (p->t > 0) ? p->t : p->m * m.hbar * m.hbar;
-    // queries per pass: as many as the budget (or 80% of free memory) allows, at most 64
     size_t per = ws_bytes(m, p->fp64, p->form);
     size_t avail;
     if (c->shared->budget) {
@@ -182,59 +249,18 @@ gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std
     int chunk = (int)std::min<size_t>(64, std::max<size_t>(1, avail / per));
     chunk = std::min(chunk, K);
     while ((int)pool.size() < chunk) pool.push_back(new QueryWs());
-    cudaEvent_t ev[8];
-    for (auto &e : ev) GH_CUDA(cudaEventCreate(&e));
-    double ms[5] = {0, 0, 0, 0, 0}, gs_ms = 0.0;
+    double ms[6] = {0, 0, 0, 0, 0, 0};
     gh_status s = GH_OK;
     for (int q0 = 0; q0 < K && s == GH_OK; q0 += chunk) {
         int kq = std::min(chunk, K - q0);
-        std::vector<QueryWs *> ws(pool.begin(), pool.begin() + kq);
-        for (int q = 0; q < kq && s == GH_OK; ++q) {
-            s = ensure_ws(c, m, *ws[q], p->fp64, p->form, p->admm_iters);
-            ws[q]->diagnostics = p->diagnostics;
-        }
-        if (s != GH_OK) break;
-        std::vector<std::vector<int32_t>> part(src.begin() + q0, src.begin() + q0 + kq);
-        cudaEventRecord(ev[0], c->stream);
-        if ((s = run_bfs(c, m, ws, part)) != GH_OK) break;
-        for (int q = 0; q < kq && s == GH_OK; ++q) s = build_layout(c, m, *ws[q], t);
-        if (s != GH_OK) break;
-        cudaEventRecord(ev[1], c->stream);
-        if ((s = run_gs(c, m, ws, p->gs_sweeps, ev[6], ev[7])) != GH_OK) break;
-        cudaEventRecord(ev[2], c->stream);
-        // no host synchronisation here: a diffusion timeout leaves every index
-        // in range, and the status word is read once the solve is done
-        for (int q = 0; q < kq && s == GH_OK; ++q) {
-            if (p->diagnostics) s = run_heat_residual(c, m, *ws[q]);
-            if (s == GH_OK) s = run_normalize(c, m, *ws[q]);
-        }
-        cudaEventRecord(ev[3], c->stream);
-        for (int q = 0; q < kq && s == GH_OK; ++q) {
-            s = (p->form == GH_FORM_FACE) ? run_face_admm(c, m, *ws[q], p->admm_iters, p->mu)
-                                          : run_edge_admm(c, m, *ws[q], p->admm_iters, p->mu);
-        }
-        cudaEventRecord(ev[4], c->stream);
-        for (int q = 0; q < kq && s == GH_OK; ++q)
-            s = run_integrate(c, m, *ws[q], d_out_dev ? d_out_dev + (size_t)(q0 + q) * m.nv : nullptr);
-        cudaEventRecord(ev[5], c->stream);
-        if (s != GH_OK) break;
-        if ((s = check_status(c, "solve")) != GH_OK) break;
-        for (int i = 0; i < 5; ++i) {
-            float x = 0;
-            cudaEventElapsedTime(&x, ev[i], ev[i + 1]);
-            ms[i] += x;
-        }
-        float xg = 0;
-        cudaEventElapsedTime(&xg, ev[6], ev[7]);
-        gs_ms += xg;
+        std::vector<Item> items(kq);
+        for (int q = 0; q < kq; ++q)
+            items[q] = Item{&m, pool[q], &src[q0 + q], p, d_out_dev ? d_out_dev + (size_t)(q0 + q) * m.nv : nullptr};
+        s = solve_items(c, items, ms);
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     if (s == GH_OK) {
         if (last_k) *last_k = std::min(K, chunk);
-        if (stage_ms6) {
-            std::copy(ms, ms + 5, stage_ms6);
-            stage_ms6[5] = gs_ms;
-        }
+        if (stage_ms6) std::copy(ms, ms + 6, stage_ms6);
     }
     return s;
 }
@@ -462,6 +488,10 @@ gh_status gh_mesh_free(gh_mesh mesh) {
     if (mesh->h.inflight.load() > 0) { set_error("mesh has serving requests in flight"); return GH_EBUSY; }
     gh_ctx_s *ctx = mesh->ctx;
     Ctx *c = &ctx->c;
+    {
+        std::lock_guard<std::mutex> lk(ctx->engine_mu);
+        if (ctx->engine) engine_forget_mesh(ctx->engine, &mesh->h.m);
+    }
     cudaStreamSynchronize(c->stream);
     for (QueryWs *w : mesh->h.ws) {
         free_ws(c, w);

@@ -402,14 +402,16 @@ bool bfs_cluster_supported(int cl) {
     return false;
 }
 
-// One breadth-first launch for all queries, with clusters of `cl` CTAs.
-static gh_status run_bfs_once(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws,
+// One breadth-first launch for all queries (query q on mesh *mq[q]), with
+// clusters of `cl` CTAs.
+static gh_status run_bfs_once(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
                               const std::vector<std::vector<int32_t>> &src, int cl) {
     cudaStream_t st = c->stream;
     int K = (int)src.size();
     std::vector<BfsArgs> args(K);
     for (int q = 0; q < K; ++q) {
         QueryWs &w = *ws[q];
+        const DevMesh &m = *mq[q];
         GH_CUDA(cudaMemsetAsync(w.level.p, 0xff, sizeof(int32_t) * m.nv, st));
         GH_CUDA(cudaMemsetAsync(w.parent.p, 0xff, sizeof(int32_t) * m.nv, st));
         GH_CUDA(cudaMemsetAsync(w.key.p, 0xff, sizeof(unsigned long long) * m.nv, st));
@@ -444,15 +446,19 @@ static gh_status run_bfs_once(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &
 // separately for single queries and batches: the first solve of each kind
 // runs every size the device supports once, timed with events, and keeps
 // the fastest (all sizes give the same sets and order, so the last run's
-// result is the solve's).
-gh_status run_bfs(Ctx *c, DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src) {
+// result is the solve's).  A batch over several meshes uses clusters of 8.
+gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
+                  const std::vector<std::vector<int32_t>> &src) {
+    for (DevMesh *x : mq)
+        if (x != mq[0]) return run_bfs_once(c, mq, ws, src, 8);
+    DevMesh &m = *mq[0];
     const int kind = src.size() > 1 ? 1 : 0;
     int cl;
     {
         std::lock_guard<std::mutex> lk(*m.rec_mu);
         cl = m.bfs_cluster[kind];
     }
-    if (cl != 0) return run_bfs_once(c, m, ws, src, cl);
+    if (cl != 0) return run_bfs_once(c, mq, ws, src, cl);
     std::vector<int> cand = {8};
     if (bfs_cluster_supported(16)) cand.push_back(16);
     cudaEvent_t e0, e1;
@@ -463,7 +469,7 @@ gh_status run_bfs(Ctx *c, DevMesh &m, std::vector<QueryWs *> &ws, const std::vec
     gh_status s = GH_OK;
     for (int x : cand) {
         cudaEventRecord(e0, c->stream);
-        if ((s = run_bfs_once(c, m, ws, src, x)) != GH_OK) break;   // synchronises the stream
+        if ((s = run_bfs_once(c, mq, ws, src, x)) != GH_OK) break;   // synchronises the stream
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
         float ms = 0.0f;

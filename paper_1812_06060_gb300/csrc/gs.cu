@@ -59,6 +59,7 @@ constexpr int kMaxDeg = 8;                                    // row entries hel
 template <class T> struct GsJob {
     int nlev;
     int nsteps;            // nlev + 2 (sweeps - 1)
+    int nsweeps;           // this query's sweeps
     int n_even;            // number of even sets; ptile0[n_even] = first tile of the odd sets
     int ntickets;          // tiles over all steps
     int zero_pos;          // a position that always holds the zero state (nreach)
@@ -149,7 +150,7 @@ __device__ __forceinline__ XVal<double> ld_state(const XVal<double> *p) {
 }
 
 // tile range [first, first + count) of job j at step s
-template <class T> __device__ __forceinline__ void step_range(const GsJob<T> &j, int s, int nsweeps, int &first,
+template <class T> __device__ __forceinline__ void step_range(const GsJob<T> &j, int s, int &first,
                                                              int &count) {
     first = 0;
     count = 0;
@@ -157,7 +158,7 @@ template <class T> __device__ __forceinline__ void step_range(const GsJob<T> &j,
     int p = s & 1;
     int ihi = min(j.nlev - 1, s);
     if ((ihi & 1) != p) --ihi;
-    int ilo = max(p, s - 2 * (nsweeps - 1));
+    int ilo = max(p, s - 2 * (j.nsweeps - 1));
     if (ilo > ihi) return;
     int jlo = (ilo - p) >> 1, jhi = (ihi - p) >> 1;
     const int32_t *pt = p ? j.ptile1 : j.ptile0;
@@ -167,12 +168,12 @@ template <class T> __device__ __forceinline__ void step_range(const GsJob<T> &j,
 }
 
 template <class T>
-__global__ void k_step_counts(const GsJob<T> *__restrict__ jobs, int q, int nsweeps, int32_t *cnt) {
+__global__ void k_step_counts(const GsJob<T> *__restrict__ jobs, int q, int32_t *cnt) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     const GsJob<T> &j = jobs[q];
     if (s >= j.nsteps) return;
     int f, n;
-    step_range(j, s, nsweeps, f, n);
+    step_range(j, s, f, n);
     cnt[s] = n;
 }
 
@@ -258,12 +259,12 @@ constexpr int kMaxJobs = 256;                 // queries per launch (larger batc
 // tile number t of job J -> descriptor and step (t < J.ntickets), walking
 // forward from the step cursor scur
 template <class T>
-__device__ __forceinline__ void lookup_tile(const GsJob<T> &J, int t, int nsweeps, int &scur, TileDesc &d, int &s,
+__device__ __forceinline__ void lookup_tile(const GsJob<T> &J, int t, int &scur, TileDesc &d, int &s,
                                             int &tile) {
     while (J.stepoff[scur + 1] <= t) ++scur;
     s = scur;
     int first, count;
-    step_range(J, s, nsweeps, first, count);
+    step_range(J, s, first, count);
     tile = first + (t - J.stepoff[s]);
     d = J.tiles[tile];
 }
@@ -289,7 +290,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // sweep k once its counter reaches (k + 1) * nt.
 template <class T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
-    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nrounds, int nsweeps, unsigned long long wait_limit_ns,
+    k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nrounds, unsigned long long wait_limit_ns,
          int *abort_flag, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage<T> *stage = reinterpret_cast<Stage<T> *>(smem_raw);
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
             int sl = 0, tidl = 0;
             if (vl) {
                 int sc = scur_job[ql];
-                lookup_tile(jobs[ql], tl, nsweeps, sc, dl, sl, tidl);
+                lookup_tile(jobs[ql], tl, sc, dl, sl, tidl);
                 atomicMax_block(&scur_job[ql], sc);   // the lane with the last tile of q sets it
             }
             __syncwarp();
@@ -490,13 +491,13 @@ template <class T> __global__ void k_zero_state(XVal<T> *a, XVal<T> *b, int n) {
     }
 }
 
-template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, int sweeps, cudaEvent_t ev0,
+template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cudaEvent_t ev0,
                                      cudaEvent_t ev1) {
     if ((int)all_ws.size() > kMaxJobs) {   // one launch per kMaxJobs queries
         for (size_t b = 0; b < all_ws.size(); b += kMaxJobs) {
             std::vector<QueryWs *> part(all_ws.begin() + b,
                                         all_ws.begin() + std::min(all_ws.size(), b + (size_t)kMaxJobs));
-            gh_status s = run_gs_t<T>(c, part, sweeps, b == 0 ? ev0 : nullptr,
+            gh_status s = run_gs_t<T>(c, part, b == 0 ? ev0 : nullptr,
                                       b + kMaxJobs >= all_ws.size() ? ev1 : nullptr);
             if (s != GH_OK) return s;
         }
@@ -513,7 +514,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
     const int grid = std::max(1, per_sm * c->num_sms / std::max(1, c->gs_share));
     std::vector<GsJob<T>> jobs(K);
     size_t soff_total = 0;
-    for (int q = 0; q < K; ++q) soff_total += (size_t)ws[q]->nlev + 2 * (size_t)sweeps + 2;
+    for (int q = 0; q < K; ++q) soff_total += (size_t)ws[q]->nlev + 2 * (size_t)ws[q]->sweeps + 2;
     int32_t *scratch = nullptr;   // per query: step counts and their prefix
     GH_CUDA(cudaMallocAsync((void **)&scratch, sizeof(int32_t) * 2 * soff_total, st));
     GsJob<T> *djobs = nullptr;
@@ -523,7 +524,8 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
         QueryWs &w = *ws[q];
         GsJob<T> j{};
         j.nlev = w.nlev;
-        j.nsteps = w.nlev + 2 * (sweeps - 1);
+        j.nsteps = w.nlev + 2 * (w.sweeps - 1);
+        j.nsweeps = w.sweeps;
         j.n_even = (w.nlev + 1) / 2;
         j.lvl_off = ptr<int32_t>(w.lvl_off);
         j.gent = ptr<Ent<T>>(w.gent);
@@ -539,7 +541,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
         j.U[1] = ptr<XVal<T>>(w.U1);
         j.zero_pos = w.nreach;
         jobs[q] = j;
-        w.final_buf = (sweeps - 1) & 1;
+        w.final_buf = (w.sweeps - 1) & 1;
     }
     GH_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(GsJob<T>) * K, cudaMemcpyHostToDevice, st));
     std::vector<int32_t> ntick(K);
@@ -548,7 +550,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
         k_zero_state<T><<<blocks_for(w.nreach + 1, 256), 256, 0, st>>>(jobs[q].U[0], jobs[q].U[1], w.nreach + 1); ++c->launches;
         GH_CUDA(cudaMemsetAsync(jobs[q].done, 0, sizeof(int32_t) * (w.nlev + 1), st));
         int32_t *cnt = const_cast<int32_t *>(jobs[q].stepoff) - soff_total;
-        k_step_counts<T><<<blocks_for(jobs[q].nsteps, 256), 256, 0, st>>>(djobs, q, sweeps, cnt); ++c->launches;
+        k_step_counts<T><<<blocks_for(jobs[q].nsteps, 256), 256, 0, st>>>(djobs, q, cnt); ++c->launches;
         gh_status s = exclusive_scan_i32(c, cnt, const_cast<int32_t *>(jobs[q].stepoff), jobs[q].nsteps, &ntick[q]);
         if (s != GH_OK) { cudaFreeAsync(djobs, st); cudaFreeAsync(scratch, st); return s; }
         jobs[q].ntickets = ntick[q];
@@ -562,7 +564,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
     int *status = c->status_dev;
     int *abort_flag = &c->bar_dev->abort;
     unsigned long long wait_limit_ns = c->wait_limit_ns;
-    void *argv[] = {(void *)&djobs,         (void *)&njobs,      (void *)&nrounds, (void *)&sweeps,
+    void *argv[] = {(void *)&djobs,         (void *)&njobs,      (void *)&nrounds,
                     (void *)&wait_limit_ns, (void *)&abort_flag, (void *)&status};
     if (ev0) cudaEventRecord(ev0, st);
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_gs<T>, dim3(grid), dim3(kThreads), argv, smem, st);
@@ -576,10 +578,9 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, in
 
 }  // namespace
 
-gh_status run_gs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, int sweeps, cudaEvent_t ev0, cudaEvent_t ev1) {
-    (void)m;
+gh_status run_gs(Ctx *c, std::vector<QueryWs *> &ws, cudaEvent_t ev0, cudaEvent_t ev1) {
     if (ws.empty()) return GH_OK;
-    return ws[0]->fp64 ? run_gs_t<double>(c, ws, sweeps, ev0, ev1) : run_gs_t<float>(c, ws, sweeps, ev0, ev1);
+    return ws[0]->fp64 ? run_gs_t<double>(c, ws, ev0, ev1) : run_gs_t<float>(c, ws, ev0, ev1);
 }
 
 }  // namespace gh

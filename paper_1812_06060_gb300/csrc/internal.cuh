@@ -173,7 +173,7 @@ struct QueryWs {
     DBuf resid;     // double [iters*2]
     DBuf e1;        // double [1]
     // host-side facts of the last run
-    int nlev = 0, nreach = 0, final_buf = 0, form = 1, admm_iters = 0, diagnostics = 0;
+    int nlev = 0, nreach = 0, final_buf = 0, form = 1, admm_iters = 0, diagnostics = 0, sweeps = 0;
     double t = 0.0;
 };
 
@@ -192,6 +192,16 @@ struct MeshH {
 // device, [K][nv] (may be null).  stage_ms6 (may be null) gets the stage times.
 gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
                      const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k);
+
+// One query of a heterogeneous batch.
+struct Item {
+    DevMesh *m;
+    QueryWs *w;
+    const std::vector<int32_t> *src;   // validated, sorted, de-duplicated
+    const gh_params *p;
+    double *d_out_dev;                 // device, [m->nv] (may be null)
+};
+gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6);
 size_t ws_bytes(const DevMesh &m, int fp64, int form);
 void free_ws(Ctx *c, QueryWs *w);
 gh_status validate_params(const gh_params *p);
@@ -210,13 +220,17 @@ gh_status exclusive_scan_u32_dev(Ctx *c, const int32_t *in, int32_t *out, int64_
 gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_dev);
 
 // bfs.cu
-gh_status run_bfs(Ctx *c, DevMesh &m, std::vector<QueryWs *> &ws, const std::vector<std::vector<int32_t>> &src);
+// breadth-first sets of every query (each on its own mesh) in one launch
+gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
+                  const std::vector<std::vector<int32_t>> &src);
 bool bfs_cluster_supported(int cl);
 gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
 
 // gs.cu
 // ev0/ev1 (may be null) are recorded on the stream right around the kernel launch
-gh_status run_gs(Ctx *c, const DevMesh &m, std::vector<QueryWs *> &ws, int sweeps, cudaEvent_t ev0, cudaEvent_t ev1);
+// one persistent diffusion launch for all queries (each with its own sweeps,
+// in QueryWs::sweeps; all of one precision)
+gh_status run_gs(Ctx *c, std::vector<QueryWs *> &ws, cudaEvent_t ev0, cudaEvent_t ev1);
 
 // stages.cu
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q);

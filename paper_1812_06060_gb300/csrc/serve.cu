@@ -3,16 +3,18 @@
 // gh_submit queues a request and returns at once.  Worker threads (two by
 // default), each with its own CUDA stream, status word and workspaces, take
 // the pending requests as they arrive: a worker admits, in arrival order,
-// the requests that share the mesh and parameters of the oldest pending one,
-// as many as the memory budget (or the device's free memory) and the batch
-// limit allow, and runs them as one batch: one breadth-first launch and one
-// persistent diffusion launch for all of them, then the per-query stages.
-// Requests that arrive while a batch is on the GPU join the next batch of
-// whichever worker frees up first, so two batches' work overlaps on the
-// device; each worker's diffusion launch takes a 1/workers share of the SMs
-// so the two can be resident together.  Results are the same as a blocking
-// gh_solve of the same request: the arithmetic of every vertex does not
-// depend on the batch it ran in.
+// the requests of the oldest pending one's precision and of a similar amount
+// of work (vertices x sweeps within a factor of 4 of it) -- on any mesh, with
+// any parameters -- as long as their workspaces fit the memory budget (or
+// the device's free memory) and the batch limit, and runs them as one batch:
+// one breadth-first launch and one persistent diffusion launch for all of
+// them (every query with its own mesh and sweep count), then the per-query
+// stages.  Requests that arrive while a batch is on the GPU join the next
+// batch of whichever worker frees up first: one worker's breadth-first,
+// layout and ADMM work overlaps the other's diffusion, whose launch takes
+// the whole GPU (a second diffusion launch waits until the first ends).  Results are the same as a
+// blocking gh_solve of the same request: the arithmetic of every vertex does
+// not depend on the batch it ran in.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,7 +44,7 @@ struct Request {
 
 struct Worker {
     Ctx c;
-    std::vector<QueryWs *> pool;
+    std::map<DevMesh *, std::vector<QueryWs *>> pools;   // workspaces kept per mesh
     DBuf dout;
     std::thread th;
 };
@@ -73,24 +75,22 @@ gh_ctx_s *gh_mesh_ctx(gh_mesh_s *m);
 
 namespace gh {
 
-static bool same_batch(const Request *a, const Request *b) {
-    return a->mesh == b->mesh && a->p.form == b->p.form && a->p.fp64 == b->p.fp64 &&
-           a->p.gs_sweeps == b->p.gs_sweeps && a->p.admm_iters == b->p.admm_iters && a->p.mu == b->p.mu &&
-           a->p.m == b->p.m && a->p.t == b->p.t && a->p.diagnostics == b->p.diagnostics;
-}
-
 static void worker_loop(Engine *E, Worker *W) {
     cudaSetDevice(W->c.device);
     while (true) {
         std::vector<Request *> batch;
+        std::vector<QueryWs *> wsq;
         {
             std::unique_lock<std::mutex> lk(E->mu);
             E->cv_work.wait(lk, [&] { return E->stop || !E->pending.empty(); });
             if (E->stop && E->pending.empty()) return;
-            Request *first = E->pending.front();
-            DevMesh &m = gh_mesh_host(first->mesh)->m;
-            // admission: requests whose workspaces fit next to what is held
-            size_t per = ws_bytes(m, first->p.fp64, first->p.form);
+            const int fp64 = E->pending.front()->p.fp64;
+            auto work = [](const Request *r) {
+                return (double)gh_mesh_host(r->mesh)->m.nv * (double)std::max(1, r->p.gs_sweeps);
+            };
+            const double w0 = work(E->pending.front());
+            // admission in arrival order: a workspace this worker already holds
+            // for the request's mesh costs nothing, a new one its size
             size_t avail;
             Shared *sh = W->c.shared;
             if (sh->budget) {
@@ -101,48 +101,64 @@ static void worker_loop(Engine *E, Worker *W) {
                 cudaMemGetInfo(&fr, &tot);
                 avail = (size_t)(0.8 * (double)fr);
             }
-            for (QueryWs *w : W->pool) avail += (w->level.p && w->cap_nv == m.nv) ? per : 0;
-            size_t kmax = std::max<size_t>(1, std::min<size_t>((size_t)E->max_batch, avail / per));
-            for (auto it = E->pending.begin(); it != E->pending.end() && batch.size() < kmax;) {
-                if (same_batch(*it, first)) {
-                    batch.push_back(*it);
-                    (*it)->state = 1;
-                    it = E->pending.erase(it);
-                } else {
+            std::map<DevMesh *, size_t> taken;
+            for (auto it = E->pending.begin(); it != E->pending.end() && (int)batch.size() < E->max_batch;) {
+                Request *r = *it;
+                const double wr = work(r);
+                if (r->p.fp64 != fp64 || wr > 4.0 * w0 || 4.0 * wr < w0) {
                     ++it;
+                    continue;
                 }
+                DevMesh *m = &gh_mesh_host(r->mesh)->m;
+                std::vector<QueryWs *> &pool = W->pools[m];
+                const size_t k = taken[m];
+                const bool reuse = k < pool.size() && pool[k]->level.p;
+                const size_t cost = reuse ? 0 : ws_bytes(*m, fp64, r->p.form);
+                if (!batch.empty() && cost > avail) break;   // the rest waits for memory
+                avail -= std::min(cost, avail);
+                if (k == pool.size()) pool.push_back(new QueryWs());
+                taken[m] = k + 1;
+                wsq.push_back(pool[k]);
+                batch.push_back(r);
+                r->state = 1;
+                it = E->pending.erase(it);
             }
         }
-        Request *r0 = batch[0];
-        DevMesh &m = gh_mesh_host(r0->mesh)->m;
-        std::vector<std::vector<int32_t>> sets;
-        for (Request *r : batch) sets.push_back(r->src);
         gh_status st = GH_OK;
         std::string err;
+        std::vector<size_t> off(batch.size() + 1, 0);
+        for (size_t q = 0; q < batch.size(); ++q) off[q + 1] = off[q] + (size_t)gh_mesh_host(batch[q]->mesh)->m.nv;
         try {
-            st = dalloc(&W->c, W->dout, sizeof(double) * (size_t)m.nv * batch.size());
-            if (st == GH_OK) st = solve_core(&W->c, m, W->pool, sets, &r0->p, ptr<double>(W->dout), nullptr, nullptr);
+            st = dalloc(&W->c, W->dout, sizeof(double) * off.back());
+            if (st == GH_OK) {
+                std::vector<Item> items(batch.size());
+                for (size_t q = 0; q < batch.size(); ++q)
+                    items[q] = Item{&gh_mesh_host(batch[q]->mesh)->m, wsq[q], &batch[q]->src, &batch[q]->p,
+                                    ptr<double>(W->dout) + off[q]};
+                st = solve_items(&W->c, items, nullptr);
+            }
             if (st != GH_OK) err = gh_last_error();
         } catch (const std::exception &ex) {
             st = GH_EDEVICE;
             err = std::string("serving worker: ") + ex.what();
         }
         if (st == GH_OK) {
-            for (size_t q = 0; q < batch.size() && st == GH_OK; ++q) {
-                try {
-                    batch[q]->d.resize(m.nv);
-                } catch (const std::exception &ex) {
-                    st = GH_ENOMEM;
-                    err = "host memory for served distances";
-                    break;
-                }
-                cudaError_t e = cudaMemcpyAsync(batch[q]->d.data(), ptr<double>(W->dout) + q * m.nv,
-                                                sizeof(double) * m.nv, cudaMemcpyDeviceToHost, W->c.stream);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(W->c.stream);
-                if (e != cudaSuccess) {
-                    st = cuda_fail(e, "copy of served distances");
-                    err = gh_last_error();
-                }
+            try {
+                for (size_t q = 0; q < batch.size(); ++q) batch[q]->d.resize(off[q + 1] - off[q]);
+            } catch (const std::exception &ex) {
+                st = GH_ENOMEM;
+                err = "host memory for served distances";
+            }
+        }
+        if (st == GH_OK) {
+            cudaError_t e = cudaSuccess;
+            for (size_t q = 0; q < batch.size() && e == cudaSuccess; ++q)
+                e = cudaMemcpyAsync(batch[q]->d.data(), ptr<double>(W->dout) + off[q], sizeof(double) * (off[q + 1] - off[q]),
+                                    cudaMemcpyDeviceToHost, W->c.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(W->c.stream);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "copy of served distances");
+                err = gh_last_error();
             }
         }
         {
@@ -167,7 +183,7 @@ static gh_status engine_start(gh_ctx_s *ctx, Engine *&out) {
     for (int i = 0; i < nw; ++i) {
         Worker *W = new Worker();
         W->c = *base;
-        W->c.gs_share = nw;
+        W->c.gs_share = 1;
         cudaError_t e = cudaStreamCreateWithFlags(&W->c.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc((void **)&W->c.status_dev, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(W->c.status_dev, 0, sizeof(int));
@@ -196,10 +212,11 @@ void engine_stop(Engine *E) {
     E->cv_work.notify_all();
     for (Worker *W : E->workers) {
         if (W->th.joinable()) W->th.join();
-        for (QueryWs *w : W->pool) {
-            free_ws(&W->c, w);
-            delete w;
-        }
+        for (auto &kv : W->pools)
+            for (QueryWs *w : kv.second) {
+                free_ws(&W->c, w);
+                delete w;
+            }
         dfree(&W->c, W->dout);
         cudaStreamDestroy(W->c.stream);
         cudaFree(W->c.status_dev);
@@ -208,6 +225,21 @@ void engine_stop(Engine *E) {
     }
     for (auto &kv : E->all) delete kv.second;
     delete E;
+}
+
+// A mesh is being freed (no request of it in flight): drop the workspaces
+// the workers keep for it.
+void engine_forget_mesh(Engine *E, DevMesh *m) {
+    std::lock_guard<std::mutex> lk(E->mu);
+    for (Worker *W : E->workers) {
+        auto it = W->pools.find(m);
+        if (it == W->pools.end()) continue;
+        for (QueryWs *w : it->second) {
+            free_ws(&W->c, w);
+            delete w;
+        }
+        W->pools.erase(it);
+    }
 }
 
 }  // namespace gh

@@ -1,0 +1,71 @@
+"""The FP32 path at the benchmark's full sizes and sweep counts against
+distances the FP64 oracle computed for the same seeded inputs
+(tests/golden/fullsize_*.json, written by make_fullsize_golden.py, which
+calls only the oracle and the input generators): the contract, relative
+error <= 1e-4 against max(|d*|, hbar), on a uniform sample of vertices, and
+the sampled vertices' breadth-first set indices bit-exact."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import meshgen
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def gh():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_06060_gb300 import build
+    build.build()
+    import paper_1812_06060_gb300 as g
+    g.load_library()
+    return g
+
+
+def _golden(name):
+    path = os.path.join(HERE, f"fullsize_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _mesh(name):
+    if name.startswith("c2-"):
+        return meshgen.workload_c2().mesh
+    return meshgen.workload_c3().mesh
+
+
+@pytest.mark.parametrize("name", ["c2-face", "c2-edge", "c3-edge"])
+def test_fp32_contract_at_full_size(gh, name):
+    gd = _golden(name)
+    mesh = _mesh(name)
+    assert mesh.nv == gd["nv"]
+    ctx = gh.Context(0)
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    try:
+        d = np.empty(mesh.nv)
+        M.solve(np.asarray(gd["sources"], np.int32), d,
+                gh.params(gs_sweeps=gd["sweeps"], form=gd["form"], m=gd["m"], admm_iters=gd["admm_iters"],
+                          mu=gd["mu"]))
+        idx = np.asarray(gd["index"])
+        ref = np.asarray(gd["d"])
+        assert np.array_equal(M.dump(gh.GH_DUMP_LEVEL)[idx], np.asarray(gd["level"]))
+        keep = ~np.isin(idx, gd["sources"])
+        err = np.abs(d[idx][keep] - ref[keep]) / np.maximum(np.abs(ref[keep]), gd["hbar"])
+        path = os.path.join(os.path.dirname(HERE), "..", "gpurun_out")
+        if os.path.isdir(path):
+            with open(os.path.join(path, "parity_errors.txt"), "a") as f:
+                f.write(f"golden {name} nv={gd['nv']} sweeps={gd['sweeps']} fp32: d max {err.max():.2e} "
+                        f"p99 {np.percentile(err, 99):.2e} over {keep.sum()} sampled vertices\n")
+        assert err.max() <= 1e-4
+    finally:
+        M.close()
+        ctx.close()

@@ -1,6 +1,7 @@
 """Serving (gh_submit / gh_poll / gh_wait): continuous batching over several
-meshes; every served result equals the same request solved alone, and
-admission by memory keeps working under a tight budget."""
+meshes, forms and sweep counts in one batch; every served result equals the
+same request solved alone, and admission by memory keeps working under a
+tight budget."""
 import threading
 import time
 
@@ -40,8 +41,9 @@ def test_served_results_equal_solo_results(gh):
         k = int(rng.random() * len(M))
         src = meshgen.random_sources(rng, meshes[k].nv, 1, 16)
         form = "face" if rng.random() < 0.5 else "edge"
-        reqs.append((k, src, form))
-    prms = {f: gh.params(gs_sweeps=150, form=f) for f in ("face", "edge")}
+        sweeps = 100 if rng.random() < 0.5 else 150
+        reqs.append((k, src, (form, sweeps)))
+    prms = {(f, n): gh.params(gs_sweeps=n, form=f) for f in ("face", "edge") for n in (100, 150)}
     ids = [None] * len(reqs)
 
     def submitter(part):
@@ -65,9 +67,9 @@ def test_served_results_equal_solo_results(gh):
         M[k].solve(src, solo, prms[form])
         assert np.array_equal(served[i], solo), f"request {i} differs from its solo solve"
     # and one of them against the oracle
-    k, src, form = reqs[0]
+    k, src, (form, sweeps) = reqs[0]
     md = oracle.mesh_data(meshes[k].V, meshes[k].F)
-    ref = oracle.solve(md, src, form, sweeps=150)
+    ref = oracle.solve(md, src, form, sweeps=sweeps)
     mask = np.ones(md.nv, bool)
     mask[src] = False
     err = np.max(np.abs(served[0][mask] - ref["d"][mask]) / np.maximum(np.abs(ref["d"][mask]), md.hbar))
