@@ -41,7 +41,7 @@ ADMM = 10
 FORMS = ("face", "edge")
 WORKLOAD = (f"jittered grid {GRID_N}x{GRID_N} (1,050,625 V, 2,097,152 F), one uniform random source, "
             f"{SWEEPS} Gauss-Seidel sweeps, {ADMM} ADMM iterations, face + edge forms (2 solves per step)")
-ORACLE_SAMPLE_SWEEPS = 40
+ORACLE_SAMPLE_SWEEPS = 150   # about 15 s of single-thread oracle work per step
 
 
 def _rank():
