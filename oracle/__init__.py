@@ -76,9 +76,9 @@ def _declare(L):
     L.orc_normalize.restype = C.c_int
     L.orc_normalize.argtypes = [I64, P, I64, P, P, P, P]
     L.orc_face_admm.restype = C.c_int
-    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, P, P, P, P]
+    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, D, D, I32, P, P, P, P, P]
     L.orc_edge_admm.restype = C.c_int
-    L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, P, P, P, P, P]
+    L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, D, D, I32, P, P, P, P, P, P]
     L.orc_integrate_face.restype = C.c_int
     L.orc_integrate_face.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
     L.orc_integrate_edge.restype = C.c_int
@@ -225,33 +225,42 @@ def normalize(md: MeshData, state) -> np.ndarray:
     return h
 
 
-def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU):
+def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None):
     """Face-based ADMM (Sec. 3.2).  Returns g [nf,3], y [nf,3,3],
-    lambda [nf,3,3] (NaN on boundary slots) and residuals [iters, 3]."""
+    lambda [nf,3,3] (NaN on boundary slots) and residuals [iterations run, 3]
+    (|r_primal|, |r_dual|, |M|_F).  eps = (eps1, eps2) stops once both
+    residuals are within |M|_F * eps (Sec. 3.2); None runs all iters."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     g = np.empty((md.nf, 3))
     y = np.empty((md.nf, 3, 3))
     lam = np.empty((md.nf, 3, 3))
     res = np.empty((max(iters, 1), 3))
+    done = C.c_int32(0)
+    e1, e2 = eps if eps is not None else (0.0, 0.0)
     _check(lib().orc_face_admm(md.nv, _p(md.P), md.nf, md.ne, _p(md.edges), _p(md.face_edge), _p(md.edge_face),
-                               _p(md.edge_slot), _p(md.Af), _p(h), iters, mu, _p(g), _p(y), _p(lam), _p(res)),
-           "orc_face_admm")
-    return g, y, lam, res[:iters]
+                               _p(md.edge_slot), _p(md.Af), _p(h), iters, mu, e1, e2, int(eps is not None), _p(g),
+                               _p(y), _p(lam), _p(res), C.byref(done)), "orc_face_admm")
+    return g, y, lam, res[:done.value]
 
 
-def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU):
+def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None):
     """Edge-based ADMM (Sec. 4.1).  Returns x [ne], w [nf,3], lambda [nf,3],
-    z [nf,3] and residuals [iters, 2]."""
+    z [nf,3] and residuals [iterations run, 2].  eps = (eps1, eps2) stops
+    once both residuals are within |Z|_F * eps (the targets' norm standing
+    in for Sec. 3.2's |M|_F); None runs all iters."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     x = np.empty(md.ne)
     w = np.empty((md.nf, 3))
     lam = np.empty((md.nf, 3))
     z = np.empty((md.nf, 3))
     res = np.empty((max(iters, 1), 2))
+    done = C.c_int32(0)
+    e1, e2 = eps if eps is not None else (0.0, 0.0)
     _check(lib().orc_edge_admm(md.nv, _p(md.P), md.nf, _p(md.F), md.ne, _p(md.edges), _p(md.flip),
                                _p(md.face_edge), _p(md.face_sign), _p(md.edge_face), _p(md.edge_slot), _p(h),
-                               iters, mu, _p(x), _p(w), _p(lam), _p(z), _p(res)), "orc_edge_admm")
-    return x, w, lam, z, res[:iters]
+                               iters, mu, e1, e2, int(eps is not None), _p(x), _p(w), _p(lam), _p(z), _p(res),
+                               C.byref(done)), "orc_edge_admm")
+    return x, w, lam, z, res[:done.value]
 
 
 def integrate_face(md: MeshData, b: BFS, g, parent=None) -> np.ndarray:
@@ -282,20 +291,21 @@ def diffusion_time(md: MeshData, m: float = 1.0) -> float:
 
 
 def solve(md: MeshData, sources, form: str = "edge", sweeps: int = 200, m: float = 1.0, t: float | None = None,
-          admm_iters: int = ADMM_ITERS, mu: float = MU) -> dict:
+          admm_iters: int = ADMM_ITERS, mu: float = MU, eps=None) -> dict:
     """Algorithm 1 end to end: Diffusion -> normalise -> Integrable ->
     Recovery, in the face form (Sec. 3) or the edge form (Sec. 4).  Returns
-    every intermediate."""
+    every intermediate.  eps = (eps1, eps2) ends the ADMM early on its
+    residuals (Sec. 3.2); the iterations run are len(out["res"])."""
     t = diffusion_time(md, m) if t is None else t
     b = bfs(md, sources)
     st = gs(md, b, t, sweeps)
     h = normalize(md, st)
     out = {"t": t, "bfs": b, "u": st, "h": h}
     if form == "face":
-        g, y, lam, res = face_admm(md, h, admm_iters, mu)
+        g, y, lam, res = face_admm(md, h, admm_iters, mu, eps)
         out.update(g=g, res=res, d=integrate_face(md, b, g))
     elif form == "edge":
-        x, w, lam, z, res = edge_admm(md, h, admm_iters, mu)
+        x, w, lam, z, res = edge_admm(md, h, admm_iters, mu, eps)
         out.update(x=x, z=z, res=res, d=integrate_edge(md, b, x))
     else:
         raise ValueError(form)

@@ -436,12 +436,16 @@ int orc_normalize(int64_t nv, const double *P, int64_t nf, const int32_t *F, con
  *   lambda: lambda_k += mu alpha_i (y_k - g_i)
  * Storage per slot [3f+k]: y and lambda (NaN on boundary slots).
  * res (nullable) receives per iteration |r_primal|_F, |r_dual|_F and |M|_F
+ * With early_stop the iterations end once |r_primal| <= |M|_F eps1 and
+ * |r_dual| <= |M|_F eps2 (Sec. 3.2); done (nullable) receives the
+ * iterations run.
  * with r_primal = M (Y - S G) and r_dual = mu M S dG.  READING: the dual
  * residual is printed with a matrix A that is never defined; it is read as M.
  */
 int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int32_t *edges,
                   const int32_t *face_edge, const int32_t *edge_face, const int32_t *edge_slot, const double *Af,
-                  const double *h, int32_t iters, double mu, double *g, double *y, double *lam, double *res) {
+                  const double *h, int32_t iters, double mu, double eps1, double eps2, int32_t early_stop,
+                  double *g, double *y, double *lam, double *res, int32_t *done) {
     (void)nv;
     double *gold = (double *)malloc(sizeof(double) * 3 * (size_t)nf);
     if (!gold) return ORC_ENOMEM;
@@ -514,7 +518,11 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
             }
         }
         if (res) { res[3 * it] = sqrt(rp); res[3 * it + 1] = sqrt(rd); res[3 * it + 2] = sqrt(mnorm2); }
+        if (done) *done = it + 1;
+        /* Sec. 3.2: stop once |r_primal| <= |M|_F eps1 and |r_dual| <= |M|_F eps2 */
+        if (early_stop && sqrt(rp) <= sqrt(mnorm2) * eps1 && sqrt(rd) <= sqrt(mnorm2) * eps2) break;
     }
+    if (done && iters <= 0) *done = 0;
     free(gold);
     return ORC_OK;
 }
@@ -533,12 +541,14 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
  *   W: w_f = (I - q q^T / 3)(x_f - lambda_f / mu), q = the face's signs
  *   X: x_e = sum_{slots of e} (z + lambda + mu w) / (|H_e| (1 + mu))  (eq. xeupdate)
  *   lambda: lambda += mu (W - R X)
- * res (nullable) receives per iteration |W - RX| and |mu R dX|.
+ * res (nullable) receives per iteration |W - RX| and |mu R dX|.  With
+ * early_stop the iteration ends once |W - RX| <= |Z|_F eps1 and
+ * |mu R dX| <= |Z|_F eps2; done (nullable) receives the iterations run.
  */
 int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int64_t ne, const int32_t *edges,
                   const uint8_t *flip, const int32_t *face_edge, const int8_t *face_sign, const int32_t *edge_face,
-                  const int32_t *edge_slot, const double *h, int32_t iters, double mu, double *x, double *w,
-                  double *lam, double *z, double *res) {
+                  const int32_t *edge_slot, const double *h, int32_t iters, double mu, double eps1, double eps2,
+                  int32_t early_stop, double *x, double *w, double *lam, double *z, double *res, int32_t *done) {
     (void)nv; (void)F;
     double *xold = (double *)malloc(sizeof(double) * (size_t)ne);
     if (!xold) return ORC_ENOMEM;
@@ -560,6 +570,11 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
         x[e] = s / n;
     }
     for (int64_t i = 0; i < 3 * nf; ++i) { w[i] = z[i]; lam[i] = 0.0; }
+    /* the scale of the edge form's residuals: |Z|_F, the norm of the targets
+       (the paper prints no thresholds for this form; read as in Sec. 3.2 with
+       |Z|_F in the place of |M|_F) */
+    double znorm2 = 0.0;
+    for (int64_t i = 0; i < 3 * nf; ++i) znorm2 += z[i] * z[i];
 
     for (int32_t it = 0; it < iters; ++it) {
         /* W-update per face */
@@ -598,7 +613,10 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
             }
         }
         if (res) { res[2 * it] = sqrt(rp); res[2 * it + 1] = sqrt(rd); }
+        if (done) *done = it + 1;
+        if (early_stop && sqrt(rp) <= sqrt(znorm2) * eps1 && sqrt(rd) <= sqrt(znorm2) * eps2) break;
     }
+    if (done && iters <= 0) *done = 0;
     free(xold);
     return ORC_OK;
 }
