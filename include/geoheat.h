@@ -71,6 +71,14 @@ typedef enum { GH_FORM_FACE = 0, GH_FORM_EDGE = 1 } gh_form;
  *  diagnostics 1: also compute the heat residual E1 (eq. HeatSolutionError)
  *              and the ADMM primal / dual residual norms of every iteration,
  *              readable with gh_debug_dump.  Default 0.
+ *  early_stop  1: end the ADMM once |r_primal| <= s * eps1 and
+ *              |r_dual| <= s * eps2 (Sec. 3.2), s = |M|_F (the square root of
+ *              the face area summed over interior-edge slots) in the face
+ *              form and |Z|_F (the norm of the target edge differences) in
+ *              the edge form, whose thresholds the paper does not print; at
+ *              most admm_iters iterations either way.  The iterations run are
+ *              readable with gh_debug_dump (GH_DUMP_ITERS).  Default 0.
+ *  eps1, eps2  the thresholds of early_stop; >= 0.  Default 1e-5 (Sec. 3.2).
  */
 typedef struct {
     double m;
@@ -81,7 +89,9 @@ typedef struct {
     int32_t form;
     int32_t fp64;
     int32_t diagnostics;
-    int32_t reserved;
+    int32_t early_stop;
+    double eps1;
+    double eps2;
 } gh_params;
 
 /* Fills *p with the defaults listed above. */
@@ -231,7 +241,8 @@ typedef enum {
     GH_DUMP_COL = 17,       /* int32 [2ne]   one-ring neighbours, ascending per row */
     GH_DUMP_RESID = 18,     /* float64 [admm_iters][2] primal, dual residual norms (diagnostics = 1) */
     GH_DUMP_E1 = 19,        /* float64 [1]   heat residual E1 (diagnostics = 1) */
-    GH_DUMP_T = 20          /* float64 [1]   diffusion time used */
+    GH_DUMP_T = 20,         /* float64 [1]   diffusion time used */
+    GH_DUMP_ITERS = 21      /* int32 [1]     ADMM iterations run (early_stop can end them before admm_iters) */
 } gh_dump_item;
 
 gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *count, int32_t *elem_bytes);

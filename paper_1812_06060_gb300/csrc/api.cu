@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cstddef>
+
 #include "internal.cuh"
 
 namespace gh {
@@ -107,7 +109,7 @@ bool is_device_ptr(const void *p) {
 void free_ws(Ctx *c, QueryWs *w) {
     DBuf *all[] = {&w->level, &w->parent, &w->pedge, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->twid, &w->gent,
                    &w->diag, &w->tiles, &w->ptile, &w->U0, &w->U1, &w->h, &w->g0, &w->g1, &w->l0, &w->l1, &w->z,
-                   &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1};
+                   &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1, &w->actl};
     for (DBuf *b : all) dfree(c, *b);
 }
 
@@ -139,7 +141,7 @@ static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int f
         A(z, es * 3 * nf); A(w, es * 3 * nf); A(lam, es * 3 * nf); A(sz, es * ne); A(x, es * ne);
     }
     A(inc, 8 * nv); A(d0, 8 * nv); A(d1, 8 * nv); A(n0, 4 * (nv + 1)); A(n1, 4 * (nv + 1));
-    A(resid, 16 * std::max(iters, 1)); A(e1, 8);
+    A(resid, 16 * std::max(iters, 1)); A(e1, 8); A(actl, sizeof(AdmmCtl));
 #undef A
     return GH_OK;
 }
@@ -151,6 +153,11 @@ gh_status validate_params(const gh_params *p) {
     if (!(p->mu > 0)) { set_error("mu must be > 0"); return GH_EINVAL; }
     if (p->form != GH_FORM_FACE && p->form != GH_FORM_EDGE) { set_error("form must be GH_FORM_FACE or GH_FORM_EDGE"); return GH_EINVAL; }
     if (!(p->t > 0) && !(p->m > 0)) { set_error("either t > 0 or m > 0 is required"); return GH_EINVAL; }
+    if (p->early_stop != 0 && p->early_stop != 1) { set_error("early_stop must be 0 or 1"); return GH_EINVAL; }
+    if (p->early_stop && !(p->eps1 >= 0 && p->eps2 >= 0 && p->eps1 < 1e300 && p->eps2 < 1e300)) {
+        set_error("eps1 and eps2 must be finite and >= 0");
+        return GH_EINVAL;
+    }
     return GH_OK;
 }
 
@@ -206,8 +213,8 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
         cudaEventRecord(ev[3], c->stream);
         for (int q = 0; q < K && s == GH_OK; ++q) {
             const gh_params *p = items[q].p;
-            s = (p->form == GH_FORM_FACE) ? run_face_admm(c, *items[q].m, *ws[q], p->admm_iters, p->mu)
-                                          : run_edge_admm(c, *items[q].m, *ws[q], p->admm_iters, p->mu);
+            s = (p->form == GH_FORM_FACE) ? run_face_admm(c, *items[q].m, *ws[q], p)
+                                          : run_edge_admm(c, *items[q].m, *ws[q], p);
         }
         cudaEventRecord(ev[4], c->stream);
         for (int q = 0; q < K && s == GH_OK; ++q) s = run_integrate(c, *items[q].m, *ws[q], items[q].d_out_dev);
@@ -351,6 +358,9 @@ void gh_params_default(gh_params *p) {
     p->form = GH_FORM_EDGE;
     p->fp64 = 0;
     p->diagnostics = 0;
+    p->early_stop = 0;
+    p->eps1 = 1e-5;
+    p->eps2 = 1e-5;
 }
 
 const char *gh_version(void) { return "geoheat 0.1 (sm_103a)"; }
@@ -569,6 +579,7 @@ gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *coun
     case GH_DUMP_E1: if (!w->diagnostics) { set_error("solve ran without diagnostics"); return GH_EINVAL; }
         n = 1; eb = 8; break;
     case GH_DUMP_T: n = 1; eb = 8; break;
+    case GH_DUMP_ITERS: n = 1; eb = 4; break;
     default: set_error("unknown dump item"); return GH_EINVAL;
     }
     *count = n;
@@ -648,6 +659,9 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out) {
     case GH_DUMP_RESID: return cp(w->resid, 8 * n);
     case GH_DUMP_E1: return cp(w->e1, 8);
     case GH_DUMP_T: std::memcpy(out, &w->t, 8); return GH_OK;
+    case GH_DUMP_ITERS:
+        GH_CUDA(cudaMemcpy(out, (const char *)w->actl.p + offsetof(AdmmCtl, iters_done), 4, cudaMemcpyDeviceToHost));
+        return GH_OK;
     default: set_error("unknown dump item"); return GH_EINVAL;
     }
 }

@@ -70,6 +70,15 @@ template <class T> struct alignas(sizeof(T) == 4 ? 8 : 16) Ent {
     T w;
 };
 
+// Early termination of the ADMM (Sec. 3.2), on the device: once an
+// iteration's residual norms meet the thresholds, `stop` is set and the
+// remaining iteration kernels return at once; iters_done counts the
+// iterations run.
+struct AdmmCtl {
+    int stop, iters_done, pad0, pad1;
+    double th[2];   // |r_primal| and |r_dual| thresholds
+};
+
 // One Gauss-Seidel tile: up to TILE consecutive queue positions of one set.
 struct alignas(16) TileDesc {
     int level, start, count, lo;      // set index, first position, positions, first position of the set
@@ -171,6 +180,7 @@ struct QueryWs {
     DBuf d0, d1;    // double [nv]
     DBuf n0, n1;    // int32 [nv]
     DBuf resid;     // double [iters*2]
+    DBuf actl;      // AdmmCtl: early termination of the ADMM
     DBuf e1;        // double [1]
     // host-side facts of the last run
     int nlev = 0, nreach = 0, final_buf = 0, form = 1, admm_iters = 0, diagnostics = 0, sweeps = 0;
@@ -234,8 +244,8 @@ gh_status run_gs(Ctx *c, std::vector<QueryWs *> &ws, cudaEvent_t ev0, cudaEvent_
 
 // stages.cu
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q);
-gh_status run_face_admm(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu);
-gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu);
+gh_status run_face_admm(Ctx *c, DevMesh &m, QueryWs &q, const gh_params *p);
+gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, const gh_params *p);
 gh_status run_integrate(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out_dev);
 gh_status run_heat_residual(Ctx *c, const DevMesh &m, QueryWs &q);
 

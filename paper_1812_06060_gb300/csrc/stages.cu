@@ -90,6 +90,75 @@ __global__ void k_normalize(int64_t nf, const int32_t *__restrict__ F, const int
     for (int c = 0; c < 3; ++c) h[3 * f + c] = (len > T(0)) ? -g[c] / len : T(0);
 }
 
+// ------------------------------------------------------------------ early termination
+
+__global__ void k_ctl_init(AdmmCtl *ctl, int iters) {
+    ctl->stop = 0;
+    ctl->iters_done = iters;
+    ctl->th[0] = ctl->th[1] = 0.0;
+}
+
+// per-block partial sums of the squared scale: the face area over every
+// interior-edge slot (|M|_F^2, Sec. 3.2) or the squared targets (|Z|_F^2)
+__global__ void __launch_bounds__(NT) k_face_mnorm2(int64_t nf, const int32_t *__restrict__ twin,
+                                                    const double *__restrict__ Af, double *part) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0;
+    if (f < nf)
+        for (int k = 0; k < 3; ++k) a += (twin[3 * f + k] >= 0) ? Af[f] : 0.0;
+    __shared__ double sh[NT];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+template <class T>
+__global__ void __launch_bounds__(NT) k_znorm2(int64_t n, const T *__restrict__ z, double *part) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double a = (i < n) ? (double)z[i] * (double)z[i] : 0.0;
+    __shared__ double sh[NT];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+// thresholds = sqrt(sum of the partials) * (eps1, eps2), summed in a fixed order
+__global__ void k_ctl_thresholds(const double *__restrict__ part, int nblocks, double eps1, double eps2,
+                                 AdmmCtl *ctl) {
+    __shared__ double sh[NT];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += NT) a += part[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double s = sqrt(sh[0]);
+        ctl->th[0] = s * eps1;
+        ctl->th[1] = s * eps2;
+    }
+}
+// after iteration it: stop once both residual norms are within the thresholds
+__global__ void k_admm_check(const double *__restrict__ res2, AdmmCtl *ctl, int it) {
+    if (!ctl->stop && res2[0] <= ctl->th[0] && res2[1] <= ctl->th[1]) {
+        ctl->stop = 1;
+        ctl->iters_done = it + 1;
+    }
+}
+// the face form's result is in buffer (iterations run) & 1: keep it in g0
+template <class T> __global__ void k_face_final(int64_t n, T *g0, const T *__restrict__ g1, const AdmmCtl *ctl) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (ctl->iters_done & 1)) g0[i] = g1[i];
+}
+
 // ------------------------------------------------------------------ face ADMM
 
 // Static per-face data of the face form (FP64 arithmetic, stored as T):
@@ -137,7 +206,8 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ twin,
                                                   const T *__restrict__ rec, const T *__restrict__ h,
                                                   const T *__restrict__ g_in, const T *__restrict__ q_in, T *g_out,
-                                                  T *q_out, T mu, double *part) {
+                                                  T *q_out, T mu, double *part, const AdmmCtl *ctl) {
+    if (ctl && ctl->stop) return;   // the residuals met the thresholds (the same for every thread)
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
     if (f < nf) {
@@ -253,7 +323,8 @@ __global__ void k_edge_init(int64_t ne, const int32_t *__restrict__ edge_face, c
 // (lambda += mu (w - x)) then the W-update w = (I - q q^T/3)(x_f - lambda/mu)
 template <class T>
 __global__ void k_edge_face_pass(int64_t nf, const int32_t *__restrict__ face_edge, const int8_t *__restrict__ sign,
-                                 const T *__restrict__ x, T *w, T *lam, T mu, int do_lambda) {
+                                 const T *__restrict__ x, T *w, T *lam, T mu, int do_lambda, const AdmmCtl *ctl) {
+    if (ctl && ctl->stop) return;
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     T v[3], q[3];
@@ -279,7 +350,8 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_edge_edge_pass(int64_t ne, const int32_t *__restrict__ edge_face,
                                                        const int32_t *__restrict__ edge_slot, const T *__restrict__ sz,
                                                        const T *__restrict__ w, const T *__restrict__ lam, T *x, T mu,
-                                                       double *part) {
+                                                       double *part, const AdmmCtl *ctl) {
+    if (ctl && ctl->stop) return;
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
     if (e < ne) {
@@ -321,8 +393,13 @@ __global__ void __launch_bounds__(NT) k_edge_edge_pass(int64_t ne, const int32_t
     }
 }
 
-// sum per-block residual partials in a fixed order: out = sqrt(sum)
-__global__ void k_resid_final(const double *__restrict__ part, int nblocks, double *out) {
+// sum per-block residual partials in a fixed order: out = sqrt(sum); NaN for
+// an iteration that an early stop skipped
+__global__ void k_resid_final(const double *__restrict__ part, int nblocks, double *out, const AdmmCtl *ctl) {
+    if (ctl && ctl->stop) {
+        if (threadIdx.x == 0) out[0] = out[1] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     __shared__ double s0[NT], s1[NT];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nblocks; i += NT) { a += part[2 * i]; b += part[2 * i + 1]; }
@@ -461,7 +538,8 @@ template <class T> gh_status face_rec(Ctx *c, DevMesh &m, const T *&out) {
     return GH_OK;
 }
 
-template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu) {
+template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu, bool early,
+                                        double eps1, double eps2) {
     cudaStream_t st = c->stream;
     unsigned nb = blocks_for(m.nf, NT);
     const T *rec = nullptr;
@@ -470,21 +548,33 @@ template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int ite
     T *g[2] = {ptr<T>(q.g0), ptr<T>(q.g1)};
     T *qq[2] = {ptr<T>(q.l0), ptr<T>(q.l1)};   // the q_k of each slot
     k_face_init<T><<<nb, NT, 0, st>>>(m.nf, ptr<T>(q.h), g[0], qq[0]); ++c->launches;
+    AdmmCtl *ctl = ptr<AdmmCtl>(q.actl);
+    k_ctl_init<<<1, 1, 0, st>>>(ctl, iters); ++c->launches;
     double *part = nullptr;
-    if (q.diagnostics) GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
+    if (q.diagnostics || early)
+        GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
+    if (early) {
+        k_face_mnorm2<<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), ptr<double>(m.Af), part); ++c->launches;
+        k_ctl_thresholds<<<1, NT, 0, st>>>(part, (int)nb, eps1, eps2, ctl); ++c->launches;
+    }
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;
         k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1],
-                                          qq[a ^ 1], (T)mu, part); ++c->launches;
-        if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it); ++c->launches; }
+                                          qq[a ^ 1], (T)mu, part, early ? ctl : nullptr); ++c->launches;
+        if (part) {
+            k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it, early ? ctl : nullptr); ++c->launches;
+        }
+        if (early) { k_admm_check<<<1, 1, 0, st>>>(ptr<double>(q.resid) + 2 * it, ctl, it); ++c->launches; }
     }
+    k_face_final<T><<<blocks_for(3 * m.nf, NT), NT, 0, st>>>(3 * m.nf, g[0], g[1], ctl); ++c->launches;
     if (part) cudaFreeAsync(part, st);
     q.admm_iters = iters;
     GH_CUDA(cudaGetLastError());
     return GH_OK;
 }
 
-template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu, bool early,
+                                        double eps1, double eps2) {
     cudaStream_t st = c->stream;
     unsigned nbf = blocks_for(m.nf, NT), nbe = blocks_for(m.ne, NT);
     Geo<T> geo = make_geo<T>(m);
@@ -492,14 +582,24 @@ template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, i
                                           ptr<T>(q.lam)); ++c->launches;
     k_edge_init<T><<<nbe, NT, 0, st>>>(m.ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot), ptr<T>(q.z),
                                        ptr<T>(q.sz), ptr<T>(q.x)); ++c->launches;
+    AdmmCtl *ctl = ptr<AdmmCtl>(q.actl);
+    k_ctl_init<<<1, 1, 0, st>>>(ctl, iters); ++c->launches;
     double *part = nullptr;
-    if (q.diagnostics) GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nbe, st));
+    const unsigned nbz = blocks_for(3 * m.nf, NT);
+    if (q.diagnostics || early)
+        GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * std::max(nbe, nbz), st));
+    if (early) {
+        k_znorm2<T><<<nbz, NT, 0, st>>>(3 * m.nf, ptr<T>(q.z), part); ++c->launches;
+        k_ctl_thresholds<<<1, NT, 0, st>>>(part, (int)nbz, eps1, eps2, ctl); ++c->launches;
+    }
+    const AdmmCtl *cx = early ? ctl : nullptr;
     for (int it = 0; it < iters; ++it) {
         k_edge_face_pass<T><<<nbf, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), ptr<int8_t>(m.face_sign),
-                                                ptr<T>(q.x), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, it > 0); ++c->launches;
+                                                ptr<T>(q.x), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, it > 0, cx); ++c->launches;
         k_edge_edge_pass<T><<<nbe, NT, 0, st>>>(m.ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
-                                                ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x), (T)mu, part); ++c->launches;
-        if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nbe, ptr<double>(q.resid) + 2 * it); ++c->launches; }
+                                                ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x), (T)mu, part, cx); ++c->launches;
+        if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nbe, ptr<double>(q.resid) + 2 * it, cx); ++c->launches; }
+        if (early) { k_admm_check<<<1, 1, 0, st>>>(ptr<double>(q.resid) + 2 * it, ctl, it); ++c->launches; }
     }
     if (part) cudaFreeAsync(part, st);
     q.admm_iters = iters;
@@ -542,7 +642,7 @@ template <class T> gh_status heat_resid_t(Ctx *c, const DevMesh &m, QueryWs &q) 
                                        part); ++c->launches;
     double *tmp = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * 2, st));
-    k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, tmp); ++c->launches;
+    k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, tmp, nullptr); ++c->launches;
     GH_CUDA(cudaMemcpyAsync(q.e1.p, tmp, sizeof(double), cudaMemcpyDeviceToDevice, st));
     cudaFreeAsync(part, st);
     cudaFreeAsync(tmp, st);
@@ -555,20 +655,17 @@ template <class T> gh_status heat_resid_t(Ctx *c, const DevMesh &m, QueryWs &q) 
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q) {
     return q.fp64 ? normalize_t<double>(c, m, q) : normalize_t<float>(c, m, q);
 }
-gh_status run_face_admm(Ctx *c, DevMesh &m, QueryWs &q, int iters, double mu) {
+gh_status run_face_admm(Ctx *c, DevMesh &m, QueryWs &q, const gh_params *p) {
     q.form = GH_FORM_FACE;
-    gh_status s = q.fp64 ? face_admm_t<double>(c, m, q, iters, mu) : face_admm_t<float>(c, m, q, iters, mu);
-    if (s != GH_OK) return s;
-    // the result of the last iteration is in buffer (iters & 1); keep it in g0
-    if (iters & 1) {
-        size_t es = q.fp64 ? sizeof(double) : sizeof(float);
-        GH_CUDA(cudaMemcpyAsync(q.g0.p, q.g1.p, es * 3 * m.nf, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    return GH_OK;
+    const bool early = p->early_stop != 0;
+    return q.fp64 ? face_admm_t<double>(c, m, q, p->admm_iters, p->mu, early, p->eps1, p->eps2)
+                  : face_admm_t<float>(c, m, q, p->admm_iters, p->mu, early, p->eps1, p->eps2);
 }
-gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, int iters, double mu) {
+gh_status run_edge_admm(Ctx *c, const DevMesh &m, QueryWs &q, const gh_params *p) {
     q.form = GH_FORM_EDGE;
-    return q.fp64 ? edge_admm_t<double>(c, m, q, iters, mu) : edge_admm_t<float>(c, m, q, iters, mu);
+    const bool early = p->early_stop != 0;
+    return q.fp64 ? edge_admm_t<double>(c, m, q, p->admm_iters, p->mu, early, p->eps1, p->eps2)
+                  : edge_admm_t<float>(c, m, q, p->admm_iters, p->mu, early, p->eps1, p->eps2);
 }
 gh_status run_integrate(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out_dev) {
     return q.fp64 ? integrate_t<double>(c, m, q, d_out_dev) : integrate_t<float>(c, m, q, d_out_dev);

@@ -339,3 +339,39 @@ def test_full_size_grid_1025(gh, ctx):
     assert r["herr"] < 1e-2 and r["gxerr"] < 5e-3
     assert r["derr"] < D_TOL_FP32
     r["M"].close()
+
+
+@pytest.mark.parametrize("form", ["face", "edge"])
+def test_admm_early_stop_matches_oracle(gh, ctx, form):
+    """Early termination of the ADMM on its residuals (Sec. 3.2): the GPU
+    runs as many iterations as the oracle and ends with its distances.  The
+    threshold sits halfway (geometrically) between two consecutive iterations'
+    dual residuals, so rounding cannot move the stop."""
+    mesh = meshgen.noisy_icosphere(4, 17)
+    src = [3]
+    md = oracle.mesh_data(mesh.V, mesh.F)
+    full = oracle.solve(md, src, form, sweeps=300, admm_iters=60)
+    res = full["res"]
+    scale = res[:, 2] if form == "face" else np.full(len(res), np.sqrt(np.sum(full["z"] ** 2)))
+    ratio = res[:, 1] / scale
+    k = next(i for i in range(8, len(ratio)) if ratio[i] < ratio[i - 1] * 0.98 and ratio[:i].min() > ratio[i - 1] * 0.999)
+    e2 = float(np.sqrt(ratio[k] * ratio[k - 1]))
+    eps = (1.0, e2)
+    ref = oracle.solve(md, src, form, sweeps=300, admm_iters=60, eps=eps)
+    kstop = len(ref["res"])
+    assert kstop == k + 1
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    try:
+        for fp64, tol in ((True, 1e-9), (False, 1e-4)):
+            d = np.empty(md.nv)
+            M.solve(np.asarray(src, np.int32), d, gh.params(gs_sweeps=300, admm_iters=60, form=form, fp64=fp64,
+                                                          eps=eps, diagnostics=True))
+            assert int(M.dump(gh.GH_DUMP_ITERS)[0]) == kstop
+            r = M.dump(gh.GH_DUMP_RESID).reshape(-1, 2)
+            assert np.all(np.isfinite(r[:kstop])) and np.all(np.isnan(r[kstop:]))
+            assert _d_err(d, ref["d"], src, md.hbar) < tol
+        # without early_stop all iterations run
+        M.solve(np.asarray(src, np.int32), np.empty(md.nv), gh.params(gs_sweeps=300, admm_iters=60, form=form))
+        assert int(M.dump(gh.GH_DUMP_ITERS)[0]) == 60
+    finally:
+        M.close()
