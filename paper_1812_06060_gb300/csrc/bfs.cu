@@ -28,6 +28,7 @@ struct BfsArgs {
     int32_t *parent;
     int32_t *pedge;
     int32_t *order;
+    int32_t *rb, *re;       // row bounds of each queue entry, recorded when its keys are offered (scratch)
     unsigned long long *key;
     int32_t *lvl_off;
     int32_t *meta;
@@ -69,37 +70,96 @@ __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
 // offers need no "already visited" test.
 //
 // One cluster of CL CTAs (8, or 16 where the device allows clusters that
-// large) walks the sets of one query.  The parents of a set (a contiguous
-// range of queue ranks) are split into CL
-// contiguous shares, one per CTA, each taken in chunks of BT ranks (one rank
-// per thread).  Per set:
-//   offers: every thread offers its parents' keys to their neighbours
-//           (64-bit atomicMin); cluster barrier;
-//   count:  every thread counts the neighbours whose key its parent holds,
-//           a block scan per chunk gives the CTA's total, published in
-//           shared memory; cluster barrier;
-//   place:  each CTA reads the totals of the lower-ranked CTAs through
-//           distributed shared memory and writes its children chunk by
-//           chunk in rank order (the scan of a chunk is redone here; the
-//           first chunk's counts are kept from the count pass); cluster
-//           barrier.
-// Every prefix involved (CTA totals, chunk totals, the block scan) runs in
-// rank order, so the queue is exactly the FIFO order.
+// large) walks the sets of one query.  Each CTA owns a contiguous range of
+// the current set's queue ranks (the ranges follow the CTA order).  Per set:
+//   count:  every thread counts the children of its parents (the neighbours
+//           whose key its parent holds), a block scan per chunk of BT ranks
+//           gives the CTA's total, published in shared memory; cluster
+//           barrier;
+//   place:  each CTA reads the lower-ranked CTAs' totals through distributed
+//           shared memory and writes its children in rank order (queue
+//           entry, set, pairing vertex and edge); the children a
+//           CTA placed are the parents it owns in the next set, so after a
+//           CTA barrier it records their row bounds and offers their keys to
+//           their neighbours (64-bit atomicMin) without waiting for the other
+//           CTAs; cluster barrier.
+// When the ownership grows lopsided (a set of at least kRebalance vertices
+// with one CTA owning more than twice its share: a single source starts in
+// one CTA), the set is split evenly instead, after one more cluster barrier.
+// Every prefix involved runs in rank order, so the queue is exactly the
+// FIFO order.
+constexpr int kRebalance = 256;
+
 __device__ __forceinline__ unsigned long long bfs_key(int r, int slot) {
     return ((unsigned long long)(unsigned)(r + 1) << 32) | (unsigned)slot;
 }
+
+// The slot loops below take a row kSlotBatch slots at a time, loading all of
+// a batch's neighbours before the dependent key loads or atomics, so a row
+// costs one round trip per level of the load chain rather than one per slot.
+constexpr int kSlotBatch = 8;
 
 // children of parent rank r (row [b, e)): count and the mask of the first 32 slots
 __device__ __forceinline__ int bfs_children(const BfsArgs &a, int r, int b, int e, unsigned &mk) {
     int k = 0;
     mk = 0;
-    for (int j = b; j < e; ++j) {
-        if (__ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b)) {
-            ++k;
-            if (j - b < 32) mk |= 1u << (j - b);
+    for (int j0 = b; j0 < e; j0 += kSlotBatch) {
+        int w[kSlotBatch];
+        unsigned long long kv[kSlotBatch];
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) w[u] = j0 + u < e ? __ldg(&a.col[j0 + u]) : -1;
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) kv[u] = w[u] >= 0 ? __ldcg(&a.key[w[u]]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) {
+            const int sl = j0 + u - b;
+            if (w[u] >= 0 && kv[u] == bfs_key(r, sl)) {
+                ++k;
+                if (sl < 32) mk |= 1u << sl;
+            }
         }
     }
     return k;
+}
+
+__device__ __forceinline__ void bfs_offer(const BfsArgs &a, int r, int b, int e) {
+    for (int j0 = b; j0 < e; j0 += kSlotBatch) {
+        int w[kSlotBatch];
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) w[u] = j0 + u < e ? __ldg(&a.col[j0 + u]) : -1;
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u)
+            if (w[u] >= 0) atomicMin(&a.key[w[u]], bfs_key(r, j0 + u - b));
+    }
+}
+
+// writes the children of parent p (rank r, row [b, e)) from queue position at on
+__device__ __forceinline__ void bfs_place(const BfsArgs &a, int nlev, int p, int r, int b, int e, unsigned mk, int at) {
+    for (int j0 = b; j0 < e; j0 += kSlotBatch) {
+        int w[kSlotBatch], ce[kSlotBatch];
+        bool ch[kSlotBatch];
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) {
+            const bool in = j0 + u < e;
+            w[u] = in ? __ldg(&a.col[j0 + u]) : -1;
+            ce[u] = in ? __ldg(&a.col_edge[j0 + u]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) {
+            const int sl = j0 + u - b;
+            ch[u] = w[u] >= 0 && (sl < 32 ? ((mk >> sl) & 1u) != 0 : __ldcg(&a.key[w[u]]) == bfs_key(r, sl));
+        }
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) {
+            if (ch[u]) {
+                a.order[at] = w[u];
+                a.level[w[u]] = nlev;
+                a.parent[w[u]] = p;
+                a.pedge[w[u]] = ce[u];
+                ++at;
+            }
+        }
+    }
 }
 
 template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *__restrict__ all) {
@@ -108,40 +168,37 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
     const int crank = (int)cluster.block_rank();
     const BfsArgs a = all[blockIdx.x / CL];
     __shared__ int s_total;
-    int lo = 0, hi = a.n0, nlev = 1;
+    int hi = a.n0, nlev = 1;
     if (crank == 0 && threadIdx.x == 0) a.lvl_off[0] = 0;
-    while (true) {
-        const int n = hi - lo;
-        const int per = (n + CL - 1) / CL;
-        const int mlo = min(hi, lo + crank * per), mhi = min(hi, mlo + per);
-        const int nchunk = (mhi - mlo + BT - 1) / BT;
-        // offers; the first chunk's row stays in registers
-        int p0 = -1, b0 = 0, e0 = 0;
-        for (int c = 0; c < nchunk; ++c) {
-            const int r = mlo + c * BT + (int)threadIdx.x;
-            if (r < mhi) {
-                const int p = __ldcg(&a.order[r]);
-                const int b = a.rowptr[p], e = a.rowptr[p + 1];
-                for (int j = b; j < e; ++j) atomicMin(&a.key[a.col[j]], bfs_key(r, j - b));
-                if (c == 0) { p0 = p; b0 = b; e0 = e; }
-            }
+    // the sources, split evenly: row bounds and offers
+    int plo, phi;
+    {
+        const int per = (a.n0 + CL - 1) / CL;
+        plo = min(a.n0, crank * per);
+        phi = min(a.n0, plo + per);
+        for (int r = plo + (int)threadIdx.x; r < phi; r += BT) {
+            const int v = a.order[r];
+            const int b = a.rowptr[v], e = a.rowptr[v + 1];
+            a.rb[r] = b;
+            a.re[r] = e;
+            bfs_offer(a, r, b, e);
         }
-        cluster.sync();
-        // count: the CTA's total over its chunks; the first chunk's counts are kept
-        int k0 = 0, ex0 = 0, tot0 = 0;
+    }
+    cluster.sync();
+    while (true) {
+        // count: the children of this CTA's parents [plo, phi); the first chunk is kept
+        const int nchunk = (phi - plo + BT - 1) / BT;
+        int p0 = -1, b0 = 0, e0 = 0, k0 = 0, ex0 = 0, tot0 = 0;
         unsigned mk0 = 0;
         int mytotal = 0;
         for (int c = 0; c < nchunk; ++c) {
-            const int r = mlo + c * BT + (int)threadIdx.x;
+            const int r = plo + c * BT + (int)threadIdx.x;
             int k = 0;
             unsigned mk = 0;
-            if (r < mhi) {
-                if (c == 0) {
-                    k = bfs_children(a, r, b0, e0, mk);
-                } else {
-                    const int p = __ldcg(&a.order[r]);
-                    k = bfs_children(a, r, a.rowptr[p], a.rowptr[p + 1], mk);
-                }
+            if (r < phi) {
+                const int b = __ldcg(&a.rb[r]), e = __ldcg(&a.re[r]);
+                k = bfs_children(a, r, b, e, mk);
+                if (c == 0) { p0 = __ldcg(&a.order[r]); b0 = b; e0 = e; }
             }
             int excl;
             const int tot = bt_scan(k, excl);
@@ -150,51 +207,60 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         }
         if (threadIdx.x == 0) s_total = mytotal;
         cluster.sync();
-        int before = 0, total = 0;
+        int before = 0, total = 0, most = 0;
         for (int q = 0; q < CL; ++q) {
             const int t = *cluster.map_shared_rank(&s_total, q);
             if (q < crank) before += t;
             total += t;
+            most = max(most, t);
+        }
+        if (total == 0) {
+            cluster.sync();   // no CTA leaves while another reads its shared memory
+            break;
         }
         // place the children: queue position hi + before + (children of this
         // CTA's earlier chunks) + (earlier parents of the chunk)
         int base_run = 0;
         for (int c = 0; c < nchunk; ++c) {
-            const int r = mlo + c * BT + (int)threadIdx.x;
+            const int r = plo + c * BT + (int)threadIdx.x;
             int p = -1, b = 0, e = 0, k = 0, excl = 0, tot = 0;
             unsigned mk = 0;
             if (c == 0) {
                 p = p0; b = b0; e = e0; k = k0; excl = ex0; tot = tot0; mk = mk0;
             } else {
-                if (r < mhi) {
+                if (r < phi) {
                     p = __ldcg(&a.order[r]);
-                    b = a.rowptr[p];
-                    e = a.rowptr[p + 1];
+                    b = __ldcg(&a.rb[r]);
+                    e = __ldcg(&a.re[r]);
                     k = bfs_children(a, r, b, e, mk);
                 }
                 tot = bt_scan(k, excl);
             }
-            if (k) {
-                int at = hi + before + base_run + excl;
-                for (int j = b; j < e; ++j) {
-                    const bool is_child = (j - b < 32) ? ((mk >> (j - b)) & 1u) != 0
-                                                       : __ldcg(&a.key[a.col[j]]) == bfs_key(r, j - b);
-                    if (is_child) {
-                        const int w = a.col[j];
-                        a.order[at++] = w;
-                        a.level[w] = nlev;
-                        a.parent[w] = p;
-                        a.pedge[w] = a.col_edge[j];
-                    }
-                }
-            }
+            if (k) bfs_place(a, nlev, p, r, b, e, mk, hi + before + base_run + excl);
             base_run += tot;
         }
+        // the next set's parents of this CTA: its own children, or an even
+        // split when one CTA would own more than twice its share
+        if (total >= kRebalance && most * CL > 2 * total) {
+            cluster.sync();   // every CTA's children are written
+            const int per = (total + CL - 1) / CL;
+            plo = min(hi + total, hi + crank * per);
+            phi = min(hi + total, plo + per);
+        } else {
+            __syncthreads();  // this CTA's children are written
+            plo = hi + before;
+            phi = plo + mytotal;
+        }
+        for (int r = plo + (int)threadIdx.x; r < phi; r += BT) {
+            const int v = __ldcg(&a.order[r]);
+            const int b = a.rowptr[v], e = a.rowptr[v + 1];
+            a.rb[r] = b;
+            a.re[r] = e;
+            bfs_offer(a, r, b, e);
+        }
         cluster.sync();
-        if (total == 0) break;
         if (crank == 0 && threadIdx.x == 0) a.lvl_off[nlev] = hi;
         ++nlev;
-        lo = hi;
         hi += total;
     }
     if (crank == 0 && threadIdx.x == 0) {
@@ -418,8 +484,10 @@ static gh_status run_bfs_once(Ctx *c, std::vector<DevMesh *> &mq, std::vector<Qu
         GH_CUDA(cudaMemcpyAsync(w.order.p, src[q].data(), sizeof(int32_t) * src[q].size(), cudaMemcpyHostToDevice, st));
         k_seed<<<blocks_for((int64_t)src[q].size(), 256), 256, 0, st>>>(ptr<int32_t>(w.level), ptr<unsigned long long>(w.key), ptr<int32_t>(w.order),
                                                                        (int)src[q].size()); ++c->launches;
+        // pos and n0 are free until the layout is built: they hold the row bounds
         args[q] = BfsArgs{ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col), ptr<int32_t>(m.col_edge), ptr<int32_t>(w.level),
                           ptr<int32_t>(w.parent), ptr<int32_t>(w.pedge), ptr<int32_t>(w.order),
+                          ptr<int32_t>(w.pos), ptr<int32_t>(w.n0),
                           ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off), ptr<int32_t>(w.meta),
                           (int32_t)src[q].size()};
     }

@@ -206,7 +206,7 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ twin,
                                                   const T *__restrict__ rec, const T *__restrict__ h,
                                                   const T *__restrict__ g_in, const T *__restrict__ q_in, T *g_out,
-                                                  T *q_out, T mu, double *part, const AdmmCtl *ctl) {
+                                                  T *q_out, T mu, double *part, const AdmmCtl *ctl, int first) {
     if (ctl && ctl->stop) return;   // the residuals met the thresholds (the same for every thread)
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
@@ -216,16 +216,18 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
         const T alpha = r4[3].x;
         T g[3], q[3][3], y[3][3];
         bool in[3];
-        for (int c = 0; c < 3; ++c) g[c] = g_in[3 * f + c];
+        // the first iteration starts from g = h and q_k = h on every slot (lambda = 0)
+        const T *gsrc = first ? h : g_in;
+        for (int c = 0; c < 3; ++c) g[c] = gsrc[3 * f + c];
         T acc[3] = {0, 0, 0};
         int n = 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            for (int c = 0; c < 3; ++c) q[k][c] = q_in[9 * f + 3 * k + c];
+            for (int c = 0; c < 3; ++c) q[k][c] = first ? g[c] : q_in[9 * f + 3 * k + c];
             const int tw = twin[3 * f + k];
             in[k] = tw >= 0;
             if (!in[k]) continue;
-            const T *qt = q_in + 9 * (int64_t)(tw >> 2) + 3 * (tw & 3);
+            const T *qt = first ? h + 3 * (int64_t)(tw >> 2) : q_in + 9 * (int64_t)(tw >> 2) + 3 * (tw & 3);
             const T eb[3] = {ek[k].x, ek[k].y, ek[k].z};
             const T proj = eb[0] * (qt[0] - q[k][0]) + eb[1] * (qt[1] - q[k][1]) + eb[2] * (qt[2] - q[k][2]);
             for (int c = 0; c < 3; ++c) {
@@ -267,20 +269,6 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
             __syncthreads();
         }
         if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
-    }
-}
-
-// g = h, lambda = 0 (q = g on every slot)
-template <class T>
-__global__ void k_face_init(int64_t nf, const T *__restrict__ h, T *g, T *q) {
-    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf) return;
-    for (int c = 0; c < 3; ++c) {
-        const T v = h[3 * f + c];
-        g[3 * f + c] = v;
-        q[9 * f + c] = v;
-        q[9 * f + 3 + c] = v;
-        q[9 * f + 6 + c] = v;
     }
 }
 
@@ -547,7 +535,9 @@ template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int ite
     if (s != GH_OK) return s;
     T *g[2] = {ptr<T>(q.g0), ptr<T>(q.g1)};
     T *qq[2] = {ptr<T>(q.l0), ptr<T>(q.l1)};   // the q_k of each slot
-    k_face_init<T><<<nb, NT, 0, st>>>(m.nf, ptr<T>(q.h), g[0], qq[0]); ++c->launches;
+    if (iters <= 0) {   // no iteration: g = h
+        GH_CUDA(cudaMemcpyAsync(g[0], ptr<T>(q.h), sizeof(T) * 3 * m.nf, cudaMemcpyDeviceToDevice, st));
+    }
     AdmmCtl *ctl = ptr<AdmmCtl>(q.actl);
     k_ctl_init<<<1, 1, 0, st>>>(ctl, iters); ++c->launches;
     double *part = nullptr;
@@ -560,7 +550,7 @@ template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int ite
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;
         k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1],
-                                          qq[a ^ 1], (T)mu, part, early ? ctl : nullptr); ++c->launches;
+                                          qq[a ^ 1], (T)mu, part, early ? ctl : nullptr, it == 0); ++c->launches;
         if (part) {
             k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it, early ? ctl : nullptr); ++c->launches;
         }
