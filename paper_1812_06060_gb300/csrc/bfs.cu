@@ -99,11 +99,11 @@ __device__ __forceinline__ unsigned long long bfs_key(int r, int slot) {
 // costs one round trip per level of the load chain rather than one per slot.
 constexpr int kSlotBatch = 8;
 
-// children of parent rank r (row [b, e)): count and the mask of the first 32 slots
-__device__ __forceinline__ int bfs_children(const BfsArgs &a, int r, int b, int e, unsigned &mk) {
+// children of parent rank r (row [b, e)) among slots [from, e): their count;
+// the first 32 slots are marked in mk
+__device__ __forceinline__ int bfs_children(const BfsArgs &a, int r, int b, int from, int e, unsigned &mk) {
     int k = 0;
-    mk = 0;
-    for (int j0 = b; j0 < e; j0 += kSlotBatch) {
+    for (int j0 = from; j0 < e; j0 += kSlotBatch) {
         int w[kSlotBatch];
         unsigned long long kv[kSlotBatch];
 #pragma unroll
@@ -122,8 +122,8 @@ __device__ __forceinline__ int bfs_children(const BfsArgs &a, int r, int b, int 
     return k;
 }
 
-__device__ __forceinline__ void bfs_offer(const BfsArgs &a, int r, int b, int e) {
-    for (int j0 = b; j0 < e; j0 += kSlotBatch) {
+__device__ __forceinline__ void bfs_offer(const BfsArgs &a, int r, int b, int from, int e) {
+    for (int j0 = from; j0 < e; j0 += kSlotBatch) {
         int w[kSlotBatch];
 #pragma unroll
         for (int u = 0; u < kSlotBatch; ++u) w[u] = j0 + u < e ? __ldg(&a.col[j0 + u]) : -1;
@@ -133,9 +133,11 @@ __device__ __forceinline__ void bfs_offer(const BfsArgs &a, int r, int b, int e)
     }
 }
 
-// writes the children of parent p (rank r, row [b, e)) from queue position at on
-__device__ __forceinline__ void bfs_place(const BfsArgs &a, int nlev, int p, int r, int b, int e, unsigned mk, int at) {
-    for (int j0 = b; j0 < e; j0 += kSlotBatch) {
+// writes the children of parent p (rank r, row [b, e)) among slots [from, e)
+// from queue position at on; returns the next position
+__device__ __forceinline__ int bfs_place(const BfsArgs &a, int nlev, int p, int r, int b, int from, int e,
+                                         unsigned mk, int at) {
+    for (int j0 = from; j0 < e; j0 += kSlotBatch) {
         int w[kSlotBatch], ce[kSlotBatch];
         bool ch[kSlotBatch];
 #pragma unroll
@@ -160,45 +162,98 @@ __device__ __forceinline__ void bfs_place(const BfsArgs &a, int nlev, int p, int
             }
         }
     }
+    return at;
+}
+
+// A thread's first parent of the current set (rank plo + threadIdx.x) stays
+// in registers from its offers to its placement: the vertex, its row and the
+// row's first kSlotBatch neighbours (after the count: the children among
+// them, else -1).
+struct Held {
+    int v, b, e;
+    int w[kSlotBatch];
+};
+
+// row bounds and offers of rank r; the first slots are kept in h
+__device__ __forceinline__ void bfs_offer_held(const BfsArgs &a, int r, Held &h) {
+    h.v = __ldcg(&a.order[r]);
+    h.b = a.rowptr[h.v];
+    h.e = a.rowptr[h.v + 1];
+    a.rb[r] = h.b;
+    a.re[r] = h.e;
+#pragma unroll
+    for (int u = 0; u < kSlotBatch; ++u) h.w[u] = h.b + u < h.e ? __ldg(&a.col[h.b + u]) : -1;
+#pragma unroll
+    for (int u = 0; u < kSlotBatch; ++u)
+        if (h.w[u] >= 0) atomicMin(&a.key[h.w[u]], bfs_key(r, u));
+    if (h.e > h.b + kSlotBatch) bfs_offer(a, r, h.b, h.b + kSlotBatch, h.e);
+}
+
+// the offers of the parents [plo, phi) of the next set
+__device__ __forceinline__ void bfs_offer_set(const BfsArgs &a, int plo, int phi, Held &h) {
+    h.v = -1;
+    h.b = h.e = 0;
+#pragma unroll
+    for (int u = 0; u < kSlotBatch; ++u) h.w[u] = -1;
+    if (plo + (int)threadIdx.x < phi) bfs_offer_held(a, plo + (int)threadIdx.x, h);
+    for (int r = plo + (int)threadIdx.x + BT; r < phi; r += BT) {
+        const int v = __ldcg(&a.order[r]);
+        const int b = a.rowptr[v], e = a.rowptr[v + 1];
+        a.rb[r] = b;
+        a.re[r] = e;
+        bfs_offer(a, r, b, b, e);
+    }
 }
 
 template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *__restrict__ all) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
-    const BfsArgs a = all[blockIdx.x / CL];
+    // the arguments stay in shared memory: registers go to the held rows
+    __shared__ BfsArgs s_args;
     __shared__ int s_total;
+    if (threadIdx.x == 0) s_args = all[blockIdx.x / CL];
+    __syncthreads();
+    const BfsArgs &a = s_args;
     int hi = a.n0, nlev = 1;
     if (crank == 0 && threadIdx.x == 0) a.lvl_off[0] = 0;
-    // the sources, split evenly: row bounds and offers
+    Held h;
+    // the sources, split evenly
     int plo, phi;
     {
         const int per = (a.n0 + CL - 1) / CL;
         plo = min(a.n0, crank * per);
         phi = min(a.n0, plo + per);
-        for (int r = plo + (int)threadIdx.x; r < phi; r += BT) {
-            const int v = a.order[r];
-            const int b = a.rowptr[v], e = a.rowptr[v + 1];
-            a.rb[r] = b;
-            a.re[r] = e;
-            bfs_offer(a, r, b, e);
-        }
+        bfs_offer_set(a, plo, phi, h);
     }
     cluster.sync();
     while (true) {
-        // count: the children of this CTA's parents [plo, phi); the first chunk is kept
+        // count: the children of this CTA's parents [plo, phi); chunk 0 from
+        // the held rows, whose children and their edges stay held
         const int nchunk = (phi - plo + BT - 1) / BT;
-        int p0 = -1, b0 = 0, e0 = 0, k0 = 0, ex0 = 0, tot0 = 0;
+        int k0 = 0, ex0 = 0, tot0 = 0;
         unsigned mk0 = 0;
         int mytotal = 0;
         for (int c = 0; c < nchunk; ++c) {
             const int r = plo + c * BT + (int)threadIdx.x;
             int k = 0;
             unsigned mk = 0;
-            if (r < phi) {
-                const int b = __ldcg(&a.rb[r]), e = __ldcg(&a.re[r]);
-                k = bfs_children(a, r, b, e, mk);
-                if (c == 0) { p0 = __ldcg(&a.order[r]); b0 = b; e0 = e; }
+            if (c == 0) {
+                unsigned long long kv[kSlotBatch];
+#pragma unroll
+                for (int u = 0; u < kSlotBatch; ++u) kv[u] = h.w[u] >= 0 ? __ldcg(&a.key[h.w[u]]) : 0ull;
+#pragma unroll
+                for (int u = 0; u < kSlotBatch; ++u) {
+                    if (h.w[u] >= 0 && kv[u] == bfs_key(r, u)) {
+                        ++k;
+                        mk |= 1u << u;
+                    } else {
+                        h.w[u] = -1;
+                    }
+                }
+                if (h.e > h.b + kSlotBatch) k += bfs_children(a, r, h.b, h.b + kSlotBatch, h.e, mk);
+            } else if (r < phi) {
+                k = bfs_children(a, r, __ldcg(&a.rb[r]), __ldcg(&a.rb[r]), __ldcg(&a.re[r]), mk);
             }
             int excl;
             const int tot = bt_scan(k, excl);
@@ -207,12 +262,20 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         }
         if (threadIdx.x == 0) s_total = mytotal;
         cluster.sync();
-        int before = 0, total = 0, most = 0;
-        for (int q = 0; q < CL; ++q) {
-            const int t = *cluster.map_shared_rank(&s_total, q);
-            if (q < crank) before += t;
-            total += t;
-            most = max(most, t);
+        // lane q of every warp reads CTA q's total; shuffles sum them
+        int before, total, most;
+        {
+            const int lane = (int)(threadIdx.x & 31);
+            const int t = lane < CL ? *cluster.map_shared_rank(&s_total, lane) : 0;
+            before = lane < crank ? t : 0;
+            total = t;
+            most = t;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                before += __shfl_xor_sync(0xffffffffu, before, o);
+                total += __shfl_xor_sync(0xffffffffu, total, o);
+                most = max(most, __shfl_xor_sync(0xffffffffu, most, o));
+            }
         }
         if (total == 0) {
             cluster.sync();   // no CTA leaves while another reads its shared memory
@@ -220,23 +283,37 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         }
         // place the children: queue position hi + before + (children of this
         // CTA's earlier chunks) + (earlier parents of the chunk)
-        int base_run = 0;
-        for (int c = 0; c < nchunk; ++c) {
-            const int r = plo + c * BT + (int)threadIdx.x;
-            int p = -1, b = 0, e = 0, k = 0, excl = 0, tot = 0;
-            unsigned mk = 0;
-            if (c == 0) {
-                p = p0; b = b0; e = e0; k = k0; excl = ex0; tot = tot0; mk = mk0;
-            } else {
-                if (r < phi) {
-                    p = __ldcg(&a.order[r]);
-                    b = __ldcg(&a.rb[r]);
-                    e = __ldcg(&a.re[r]);
-                    k = bfs_children(a, r, b, e, mk);
+        if (k0) {
+            int at = hi + before + ex0;
+            int ce[kSlotBatch];
+#pragma unroll
+            for (int u = 0; u < kSlotBatch; ++u) ce[u] = h.w[u] >= 0 ? __ldg(&a.col_edge[h.b + u]) : -1;
+#pragma unroll
+            for (int u = 0; u < kSlotBatch; ++u) {
+                if (h.w[u] >= 0) {
+                    a.order[at] = h.w[u];
+                    a.level[h.w[u]] = nlev;
+                    a.parent[h.w[u]] = h.v;
+                    a.pedge[h.w[u]] = ce[u];
+                    ++at;
                 }
-                tot = bt_scan(k, excl);
             }
-            if (k) bfs_place(a, nlev, p, r, b, e, mk, hi + before + base_run + excl);
+            if (h.e > h.b + kSlotBatch)
+                bfs_place(a, nlev, h.v, plo + (int)threadIdx.x, h.b, h.b + kSlotBatch, h.e, mk0, at);
+        }
+        int base_run = tot0;
+        for (int c = 1; c < nchunk; ++c) {
+            const int r = plo + c * BT + (int)threadIdx.x;
+            int p = -1, b = 0, e = 0, k = 0, excl = 0;
+            unsigned mk = 0;
+            if (r < phi) {
+                p = __ldcg(&a.order[r]);
+                b = __ldcg(&a.rb[r]);
+                e = __ldcg(&a.re[r]);
+                k = bfs_children(a, r, b, b, e, mk);
+            }
+            const int tot = bt_scan(k, excl);
+            if (k) bfs_place(a, nlev, p, r, b, b, e, mk, hi + before + base_run + excl);
             base_run += tot;
         }
         // the next set's parents of this CTA: its own children, or an even
@@ -251,13 +328,7 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
             plo = hi + before;
             phi = plo + mytotal;
         }
-        for (int r = plo + (int)threadIdx.x; r < phi; r += BT) {
-            const int v = __ldcg(&a.order[r]);
-            const int b = a.rowptr[v], e = a.rowptr[v + 1];
-            a.rb[r] = b;
-            a.re[r] = e;
-            bfs_offer(a, r, b, e);
-        }
+        bfs_offer_set(a, plo, phi, h);
         cluster.sync();
         if (crank == 0 && threadIdx.x == 0) a.lvl_off[nlev] = hi;
         ++nlev;
