@@ -157,15 +157,17 @@ def stage_bytes(nv: int, ne: int, nf: int, sweeps: int, iters: int, form: str, n
         layout's column, edge id, theta, position and the written entry)
       diffusion: see gs_bytes
       normalise: 66 per face (face, positions, state, gradient operator, h)
-      face ADMM: 60 per face to initialise, 154 per face and iteration (g, lambda
-        read and written, h, face edges, twins, area, edge vectors)
+      face ADMM: 154 per face and iteration (g, lambda read and written, h, face
+        edges, twins, area, edge vectors shared by the edge's two faces), less
+        48 per face for the first iteration, which starts from g = h, lambda = 0
+        and reads h in their place
       edge ADMM: 78 per face + 32 per edge to initialise, per iteration 69 per
         face (face pass: x, lambda, w, signs) + 44 per edge (edge pass)
       integration: 64 (edge form) or 112 (face form) per vertex for the
         increments, 36 per vertex for each of ceil(log2 L) jumping rounds"""
     import math
     rows = 2 * ne
-    adm = (60 * nf + iters * 154 * nf) if form == "face" else (78 * nf + 32 * ne + iters * (69 * nf + 44 * ne))
+    adm = (max(iters, 1) * 154 * nf - 48 * nf) if form == "face" else (78 * nf + 32 * ne + iters * (69 * nf + 44 * ne))
     rounds = max(1, math.ceil(math.log2(max(nlev, 2))))
     return {"bfs_layout": 88 * nv + 52 * rows, "diffusion": gs_bytes(nv, ne, sweeps), "normalize": 66 * nf,
             "admm": adm, "integrate": (64 if form == "edge" else 112) * nv + 36 * nv * rounds}
