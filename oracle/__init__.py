@@ -8,7 +8,8 @@ it with gcc, loads it with ctypes and chains the steps of Algorithm 1.
 
 Parity status of each function (pins in tests/test_oracle_*.py):
   connectivity, geometry, bfs, gs, normalize, face_admm, edge_admm,
-  integrate_face, integrate_edge: pinned.
+  integrate_face, integrate_edge, source_paths, path_constraints and the
+  path-constrained ADMM: pinned.
 """
 from __future__ import annotations
 
@@ -76,9 +77,10 @@ def _declare(L):
     L.orc_normalize.restype = C.c_int
     L.orc_normalize.argtypes = [I64, P, I64, P, P, P, P]
     L.orc_face_admm.restype = C.c_int
-    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, D, D, I32, P, P, P, P, P]
+    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P, P, P]
     L.orc_edge_admm.restype = C.c_int
-    L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, D, D, I32, P, P, P, P, P, P]
+    L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P,
+                                P, P, P]
     L.orc_integrate_face.restype = C.c_int
     L.orc_integrate_face.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
     L.orc_integrate_edge.restype = C.c_int
@@ -225,12 +227,15 @@ def normalize(md: MeshData, state) -> np.ndarray:
     return h
 
 
-def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None):
+def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
     """Face-based ADMM (Sec. 3.2).  Returns g [nf,3], y [nf,3,3],
     lambda [nf,3,3] (NaN on boundary slots) and residuals [iterations run, 3]
     (|r_primal|, |r_dual|, |M|_F).  eps = (eps1, eps2) stops once both
-    residuals are within |M|_F * eps (Sec. 3.2); None runs all iters."""
+    residuals are within |M|_F * eps (Sec. 3.2); None runs all iters.
+    pc = path_constraints(md, sources, "face") adds the multi-source
+    constraints of Sec. 5.2."""
     h = np.ascontiguousarray(h, dtype=np.float64)
+    npc, off, var, coef = _pc_args(pc, 3)
     g = np.empty((md.nf, 3))
     y = np.empty((md.nf, 3, 3))
     lam = np.empty((md.nf, 3, 3))
@@ -238,17 +243,21 @@ def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None):
     done = C.c_int32(0)
     e1, e2 = eps if eps is not None else (0.0, 0.0)
     _check(lib().orc_face_admm(md.nv, _p(md.P), md.nf, md.ne, _p(md.edges), _p(md.face_edge), _p(md.edge_face),
-                               _p(md.edge_slot), _p(md.Af), _p(h), iters, mu, e1, e2, int(eps is not None), _p(g),
-                               _p(y), _p(lam), _p(res), C.byref(done)), "orc_face_admm")
+                               _p(md.edge_slot), _p(md.Af), _p(h), iters, mu, e1, e2, int(eps is not None), npc,
+                               _p(off), _p(var), _p(coef), _p(g), _p(y), _p(lam), _p(res), C.byref(done)),
+           "orc_face_admm")
     return g, y, lam, res[:done.value]
 
 
-def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None):
+def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
     """Edge-based ADMM (Sec. 4.1).  Returns x [ne], w [nf,3], lambda [nf,3],
     z [nf,3] and residuals [iterations run, 2].  eps = (eps1, eps2) stops
     once both residuals are within |Z|_F * eps (the targets' norm standing
-    in for Sec. 3.2's |M|_F); None runs all iters."""
+    in for Sec. 3.2's |M|_F); None runs all iters.  pc =
+    path_constraints(md, sources, "edge") adds the multi-source constraints
+    of Sec. 5.2."""
     h = np.ascontiguousarray(h, dtype=np.float64)
+    npc, off, var, coef = _pc_args(pc, 1)
     x = np.empty(md.ne)
     w = np.empty((md.nf, 3))
     lam = np.empty((md.nf, 3))
@@ -258,9 +267,99 @@ def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None):
     e1, e2 = eps if eps is not None else (0.0, 0.0)
     _check(lib().orc_edge_admm(md.nv, _p(md.P), md.nf, _p(md.F), md.ne, _p(md.edges), _p(md.flip),
                                _p(md.face_edge), _p(md.face_sign), _p(md.edge_face), _p(md.edge_slot), _p(h),
-                               iters, mu, e1, e2, int(eps is not None), _p(x), _p(w), _p(lam), _p(z), _p(res),
-                               C.byref(done)), "orc_edge_admm")
+                               iters, mu, e1, e2, int(eps is not None), npc, _p(off), _p(var), _p(coef), _p(x),
+                               _p(w), _p(lam), _p(z), _p(res), C.byref(done)), "orc_edge_admm")
     return x, w, lam, z, res[:done.value]
+
+
+@dataclass
+class PathConstraints:
+    """One linear constraint per path (Sec. 5.2): entries [off[j], off[j+1])
+    of constraint j, each a variable (edge id, or face id) and a coefficient
+    (the sign, or the 3-vector of the path's edge)."""
+    off: np.ndarray
+    var: np.ndarray
+    coef: np.ndarray
+    paths: list
+
+
+def source_paths(md: MeshData, sources) -> list:
+    """Paths along edges from the first source to each other source
+    (Sec. 5.2).  READING: the paper asks for shortest paths along edges; here
+    a path has the fewest edges, the one a breadth-first traversal from the
+    first (lowest-index) source alone gives by following each vertex's FIFO
+    pairing vertex (eq. VertexSets, Sec. 3.3).  Any path between two sources
+    gives a valid constraint (the exact distance is 0 at both ends), so the
+    choice only selects which one is imposed.  Each path is a list of steps
+    (p, v) in the direction first source -> other source; a source that the
+    first cannot reach gets an empty path."""
+    src = sorted(set(int(s) for s in np.atleast_1d(sources)))
+    if len(src) < 2:
+        return []
+    b = bfs(md, [src[0]])
+    paths = []
+    for sj in src[1:]:
+        steps = []
+        v = sj
+        if b.level[v] >= 0:
+            while b.level[v] > 0:
+                p = int(b.parent[v])
+                steps.append((p, v))
+                v = p
+            steps.reverse()
+        paths.append(steps)
+    return paths
+
+
+def _edge_id(md: MeshData, a: int, b: int) -> int:
+    for j in range(md.rowptr[a], md.rowptr[a + 1]):
+        if md.col[j] == b:
+            return int(md.col_edge[j])
+    raise ValueError(f"{a} and {b} are not adjacent")
+
+
+def path_constraints(md: MeshData, sources, form: str) -> PathConstraints:
+    """The constraints of the paths of ``source_paths``:
+    edge form (eq. MultiSourceConstraintEdgeBased): sum s_e x_e = 0, s_e = +1
+      where the path runs from tail to head of the edge's orientation
+      halfedge, -1 against it;
+    face form (eq. MultiSourceConstraint): sum e_j . g_f = 0, e_j the vector
+      of the path's edge in the path's direction and f the edge's adjacent
+      face of lowest index (READING: the paper leaves the choice among the
+      adjacent faces open)."""
+    paths = source_paths(md, sources)
+    off = [0]
+    var, coef = [], []
+    for steps in paths:
+        for p, v in steps:
+            e = _edge_id(md, p, v)
+            if form == "edge":
+                a, b = int(md.edges[e, 0]), int(md.edges[e, 1])
+                tail = b if (md.flip is not None and md.flip[e]) else a
+                var.append(e)
+                coef.append([1.0 if p == tail else -1.0])
+            elif form == "face":
+                var.append(int(md.edge_face[e, 0]))
+                coef.append(list(md.P[v] - md.P[p]))
+            else:
+                raise ValueError(form)
+        off.append(len(var))
+    dim = 1 if form == "edge" else 3
+    return PathConstraints(np.asarray(off, np.int32), np.asarray(var, np.int32),
+                           np.asarray(coef, np.float64).reshape(-1, dim), paths)
+
+
+def _pc_args(pc, dim):
+    if pc is None or len(pc.off) < 2:
+        z = np.zeros(1, np.int32)
+        return 0, z, z, np.zeros(dim)
+    if pc.coef.shape[1] != dim:
+        raise ValueError("path constraints of the other form")
+    coef = np.ascontiguousarray(pc.coef, dtype=np.float64)
+    if coef.size == 0:
+        coef = np.zeros(dim)
+    var = pc.var if pc.var.size else np.zeros(1, np.int32)
+    return len(pc.off) - 1, np.ascontiguousarray(pc.off), np.ascontiguousarray(var), coef
 
 
 def integrate_face(md: MeshData, b: BFS, g, parent=None) -> np.ndarray:
@@ -291,21 +390,25 @@ def diffusion_time(md: MeshData, m: float = 1.0) -> float:
 
 
 def solve(md: MeshData, sources, form: str = "edge", sweeps: int = 200, m: float = 1.0, t: float | None = None,
-          admm_iters: int = ADMM_ITERS, mu: float = MU, eps=None) -> dict:
+          admm_iters: int = ADMM_ITERS, mu: float = MU, eps=None, path_constraints_on: bool = False) -> dict:
     """Algorithm 1 end to end: Diffusion -> normalise -> Integrable ->
     Recovery, in the face form (Sec. 3) or the edge form (Sec. 4).  Returns
     every intermediate.  eps = (eps1, eps2) ends the ADMM early on its
-    residuals (Sec. 3.2); the iterations run are len(out["res"])."""
+    residuals (Sec. 3.2); the iterations run are len(out["res"]).
+    path_constraints_on adds the multi-source constraints (Sec. 5.2)."""
     t = diffusion_time(md, m) if t is None else t
     b = bfs(md, sources)
     st = gs(md, b, t, sweeps)
     h = normalize(md, st)
     out = {"t": t, "bfs": b, "u": st, "h": h}
+    pc = path_constraints(md, sources, form) if path_constraints_on else None
+    if pc is not None:
+        out["pc"] = pc
     if form == "face":
-        g, y, lam, res = face_admm(md, h, admm_iters, mu, eps)
+        g, y, lam, res = face_admm(md, h, admm_iters, mu, eps, pc)
         out.update(g=g, res=res, d=integrate_face(md, b, g))
     elif form == "edge":
-        x, w, lam, z, res = edge_admm(md, h, admm_iters, mu, eps)
+        x, w, lam, z, res = edge_admm(md, h, admm_iters, mu, eps, pc)
         out.update(x=x, z=z, res=res, d=integrate_edge(md, b, x))
     else:
         raise ValueError(form)

@@ -418,6 +418,138 @@ int orc_normalize(int64_t nv, const double *P, int64_t nf, const int32_t *F, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* Multi-source path constraints (Sec. 5.2, eq. MultiSourceConstraint,       */
+/* eq. MultiSourceConstraintEdgeBased)                                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * npc linear constraints sum_i c_i . v_{var_i} = 0 on the variables of one
+ * ADMM block: the edge differences x (dim 1) or the face gradients g (dim 3).
+ * The entries of constraint j are [off[j], off[j+1]): variable var[i],
+ * coefficient coef[dim i .. dim i + dim).
+ *
+ * READING: Sec. 5.2 says only that the extended problem stays convex and is
+ * solved by ADMM.  Here the constraints join the block they act on.  That
+ * block's subproblem is a separable quadratic 1/2 sum_v D_v |v - vhat_v|^2
+ * around its unconstrained update vhat (D_e = |H_e| (1 + mu) for x, from the
+ * objective 1/2 sum (x - z)^2 and the penalty; D_f = A_f (2 + mu n_f) for g,
+ * from A_f |g - h|^2 and the M-weighted penalty over the face's n_f interior
+ * slots).  Its minimiser under C v = 0 solves the KKT system:
+ *   v = vhat - D^-1 C^T nu,   (C D^-1 C^T) nu = C vhat.
+ * The Gram matrix C D^-1 C^T is factored once (Cholesky); a constraint whose
+ * pivot is at most 1e-12 of its diagonal entry depends on the earlier ones
+ * (or is empty) and is dropped: nu_j = 0.
+ */
+typedef struct {
+    int32_t npc, dim, nu;  /* constraints, values per variable, distinct variables */
+    int32_t *uvar;         /* [nu] the variable of each distinct entry */
+    double *ucoef;         /* [nu][npc][dim] coefficients summed per variable */
+    double *dinv;          /* [nu] 1 / D_v */
+    double *L;             /* [npc][npc] lower Cholesky factor of the Gram matrix */
+    int32_t *drop;         /* [npc] */
+} orc_pc;
+
+static void pc_free(orc_pc *pc) {
+    free(pc->uvar); free(pc->ucoef); free(pc->dinv); free(pc->L); free(pc->drop);
+    memset(pc, 0, sizeof(*pc));
+}
+
+/* the distinct variables of the entries (in order of first appearance) and
+ * their coefficient rows; nvar = the block's variable count */
+static int pc_build(orc_pc *pc, int64_t nvar, int32_t npc, int32_t dim, const int32_t *off, const int32_t *var,
+                    const double *coef) {
+    memset(pc, 0, sizeof(*pc));
+    pc->npc = npc;
+    pc->dim = dim;
+    if (npc <= 0) return ORC_OK;
+    int32_t nent = off[npc];
+    int32_t *slot = (int32_t *)malloc(sizeof(int32_t) * (size_t)nvar);
+    pc->uvar = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nent > 0 ? nent : 1));
+    pc->ucoef = (double *)calloc((size_t)(nent > 0 ? nent : 1) * npc * dim, sizeof(double));
+    pc->dinv = (double *)malloc(sizeof(double) * (size_t)(nent > 0 ? nent : 1));
+    pc->L = (double *)calloc((size_t)npc * npc, sizeof(double));
+    pc->drop = (int32_t *)calloc((size_t)npc, sizeof(int32_t));
+    if (!slot || !pc->uvar || !pc->ucoef || !pc->dinv || !pc->L || !pc->drop) {
+        free(slot);
+        pc_free(pc);
+        return ORC_ENOMEM;
+    }
+    for (int64_t v = 0; v < nvar; ++v) slot[v] = -1;
+    for (int32_t j = 0; j < npc; ++j) {
+        for (int32_t i = off[j]; i < off[j + 1]; ++i) {
+            int32_t v = var[i];
+            if (v < 0 || v >= nvar) { free(slot); pc_free(pc); return ORC_EINVAL; }
+            if (slot[v] < 0) { slot[v] = pc->nu; pc->uvar[pc->nu++] = v; }
+            for (int c = 0; c < dim; ++c)
+                pc->ucoef[((size_t)slot[v] * npc + j) * dim + c] += coef[(size_t)dim * i + c];
+        }
+    }
+    free(slot);
+    return ORC_OK;
+}
+
+/* Gram matrix G_jk = sum_v c_vj . c_vk / D_v and its Cholesky factor
+ * (dinv must be filled) */
+static void pc_factor(orc_pc *pc) {
+    int32_t n = pc->npc, dim = pc->dim;
+    double *G = (double *)calloc((size_t)n * n + 1, sizeof(double));
+    for (int32_t u = 0; u < pc->nu; ++u)
+        for (int32_t j = 0; j < n; ++j)
+            for (int32_t k = 0; k < n; ++k) {
+                double s = 0.0;
+                for (int c = 0; c < dim; ++c)
+                    s += pc->ucoef[((size_t)u * n + j) * dim + c] * pc->ucoef[((size_t)u * n + k) * dim + c];
+                G[j * n + k] += s * pc->dinv[u];
+            }
+    for (int32_t j = 0; j < n; ++j) {
+        double d = G[j * n + j];
+        for (int32_t m = 0; m < j; ++m) d -= pc->L[j * n + m] * pc->L[j * n + m];
+        if (!(d > 1e-12 * G[j * n + j])) { pc->drop[j] = 1; continue; }   /* row j of L stays 0 */
+        double ljj = sqrt(d);
+        pc->L[j * n + j] = ljj;
+        for (int32_t k = j + 1; k < n; ++k) {
+            double s = G[k * n + j];
+            for (int32_t m = 0; m < j; ++m) s -= pc->L[k * n + m] * pc->L[j * n + m];
+            pc->L[k * n + j] = s / ljj;
+        }
+    }
+    free(G);
+}
+
+/* v <- vhat - D^-1 C^T nu with (C D^-1 C^T) nu = C vhat; vals holds vhat */
+static void pc_project(const orc_pc *pc, double *vals) {
+    int32_t n = pc->npc, dim = pc->dim;
+    if (n <= 0) return;
+    double r[64], nu[64];
+    for (int32_t j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int32_t u = 0; u < pc->nu; ++u)
+            for (int c = 0; c < dim; ++c)
+                s += pc->ucoef[((size_t)u * n + j) * dim + c] * vals[(size_t)dim * pc->uvar[u] + c];
+        r[j] = s;
+    }
+    /* L L^T nu = r, dropped constraints held at 0 */
+    for (int32_t j = 0; j < n; ++j) {
+        if (pc->drop[j]) { nu[j] = 0.0; continue; }
+        double s = r[j];
+        for (int32_t m = 0; m < j; ++m) s -= pc->L[j * n + m] * nu[m];
+        nu[j] = s / pc->L[j * n + j];
+    }
+    for (int32_t j = n - 1; j >= 0; --j) {
+        if (pc->drop[j]) { nu[j] = 0.0; continue; }
+        double s = nu[j];
+        for (int32_t m = j + 1; m < n; ++m) s -= pc->L[m * n + j] * nu[m];
+        nu[j] = s / pc->L[j * n + j];
+    }
+    for (int32_t u = 0; u < pc->nu; ++u)
+        for (int c = 0; c < dim; ++c) {
+            double s = 0.0;
+            for (int32_t j = 0; j < n; ++j) s += pc->ucoef[((size_t)u * n + j) * dim + c] * nu[j];
+            vals[(size_t)dim * pc->uvar[u] + c] -= pc->dinv[u] * s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Face-based integrable gradient field by ADMM (Sec. 3.2)                   */
 /* ------------------------------------------------------------------------ */
 
@@ -445,10 +577,22 @@ int orc_normalize(int64_t nv, const double *P, int64_t nf, const int32_t *F, con
 int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int32_t *edges,
                   const int32_t *face_edge, const int32_t *edge_face, const int32_t *edge_slot, const double *Af,
                   const double *h, int32_t iters, double mu, double eps1, double eps2, int32_t early_stop,
+                  int32_t npc, const int32_t *pc_off, const int32_t *pc_var, const double *pc_coef,
                   double *g, double *y, double *lam, double *res, int32_t *done) {
     (void)nv;
+    if (npc < 0 || npc > 64) return ORC_EINVAL;
+    orc_pc pc;
+    int rc = pc_build(&pc, nf, npc, 3, pc_off, pc_var, pc_coef);
+    if (rc != ORC_OK) return rc;
+    for (int32_t u = 0; u < pc.nu; ++u) {   /* D_f = A_f (2 + mu n_f) */
+        int64_t f = pc.uvar[u];
+        int n = 0;
+        for (int k = 0; k < 3; ++k) n += edge_face[2 * face_edge[3 * f + k] + 1] >= 0;
+        pc.dinv[u] = 1.0 / (Af[f] * (2.0 + mu * n));
+    }
+    pc_factor(&pc);
     double *gold = (double *)malloc(sizeof(double) * 3 * (size_t)nf);
-    if (!gold) return ORC_ENOMEM;
+    if (!gold) { pc_free(&pc); return ORC_ENOMEM; }
     for (int64_t f = 0; f < nf; ++f)
         for (int k = 0; k < 3; ++k)
             for (int c = 0; c < 3; ++c) { y[9 * f + 3 * k + c] = NAN; lam[9 * f + 3 * k + c] = NAN; }
@@ -502,6 +646,8 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
             }
             for (int c = 0; c < 3; ++c) g[3 * f + c] = (2.0 * h[3 * f + c] + mu * acc[c]) / (2.0 + mu * n);
         }
+        /* the multi-source path constraints, if any, as part of the G-update */
+        pc_project(&pc, g);
         /* lambda-update, and the residual norms */
         double rp = 0.0, rd = 0.0;
         for (int64_t f = 0; f < nf; ++f) {
@@ -524,6 +670,7 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
     }
     if (done && iters <= 0) *done = 0;
     free(gold);
+    pc_free(&pc);
     return ORC_OK;
 }
 
@@ -548,10 +695,21 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
 int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int64_t ne, const int32_t *edges,
                   const uint8_t *flip, const int32_t *face_edge, const int8_t *face_sign, const int32_t *edge_face,
                   const int32_t *edge_slot, const double *h, int32_t iters, double mu, double eps1, double eps2,
-                  int32_t early_stop, double *x, double *w, double *lam, double *z, double *res, int32_t *done) {
+                  int32_t early_stop, int32_t npc, const int32_t *pc_off, const int32_t *pc_var,
+                  const double *pc_coef, double *x, double *w, double *lam, double *z, double *res, int32_t *done) {
     (void)nv; (void)F;
+    if (npc < 0 || npc > 64) return ORC_EINVAL;
+    orc_pc pc;
+    int rc = pc_build(&pc, ne, npc, 1, pc_off, pc_var, pc_coef);
+    if (rc != ORC_OK) return rc;
+    for (int32_t u = 0; u < pc.nu; ++u) {   /* D_e = |H_e| (1 + mu) */
+        int64_t e = pc.uvar[u];
+        int n = (edge_face[2 * e] >= 0) + (edge_face[2 * e + 1] >= 0);
+        pc.dinv[u] = 1.0 / (n * (1.0 + mu));
+    }
+    pc_factor(&pc);
     double *xold = (double *)malloc(sizeof(double) * (size_t)ne);
-    if (!xold) return ORC_ENOMEM;
+    if (!xold) { pc_free(&pc); return ORC_ENOMEM; }
     for (int64_t f = 0; f < nf; ++f) {
         for (int k = 0; k < 3; ++k) {
             int64_t e = face_edge[3 * f + k];
@@ -600,6 +758,8 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
             }
             x[e] = s / (n * (1.0 + mu));
         }
+        /* the multi-source path constraints, if any, as part of the X-update */
+        pc_project(&pc, x);
         /* lambda-update per face slot, and the residual norms */
         double rp = 0.0, rd = 0.0;
         for (int64_t f = 0; f < nf; ++f) {
@@ -618,6 +778,7 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
     }
     if (done && iters <= 0) *done = 0;
     free(xold);
+    pc_free(&pc);
     return ORC_OK;
 }
 
