@@ -79,6 +79,16 @@ typedef enum { GH_FORM_FACE = 0, GH_FORM_EDGE = 1 } gh_form;
  *              most admm_iters iterations either way.  The iterations run are
  *              readable with gh_debug_dump (GH_DUMP_ITERS).  Default 0.
  *  eps1, eps2  the thresholds of early_stop; >= 0.  Default 1e-5 (Sec. 3.2).
+ *  path_constraints  1: with two or more sources, also make the line
+ *              integral of the optimised field vanish along a path from the
+ *              first (lowest-index) source to each other source (Sec. 5.2,
+ *              eq. MultiSourceConstraint, eq. MultiSourceConstraintEdgeBased).
+ *              The paths are the fewest-edge ones of a breadth-first
+ *              traversal from the first source alone (its FIFO pairing);
+ *              the constraints act inside the G (face form) or X (edge form)
+ *              update, whose minimiser under them is a projection through a
+ *              small Gram system.  At most 32 sources (GH_EINVAL otherwise).
+ *              No effect with one source.  Default 0.
  */
 typedef struct {
     double m;
@@ -92,6 +102,7 @@ typedef struct {
     int32_t early_stop;
     double eps1;
     double eps2;
+    int32_t path_constraints;
 } gh_params;
 
 /* Fills *p with the defaults listed above. */
@@ -242,7 +253,10 @@ typedef enum {
     GH_DUMP_RESID = 18,     /* float64 [admm_iters][2] primal, dual residual norms (diagnostics = 1) */
     GH_DUMP_E1 = 19,        /* float64 [1]   heat residual E1 (diagnostics = 1) */
     GH_DUMP_T = 20,         /* float64 [1]   diffusion time used */
-    GH_DUMP_ITERS = 21      /* int32 [1]     ADMM iterations run (early_stop can end them before admm_iters) */
+    GH_DUMP_ITERS = 21,     /* int32 [1]     ADMM iterations run (early_stop can end them before admm_iters) */
+    GH_DUMP_PC_OFF = 22,    /* int32 [npc+1] path constraints: entries of constraint j are [off[j], off[j+1]) */
+    GH_DUMP_PC_VAR = 23,    /* int32 [n]     constrained variable of each entry: edge id (edge form), face id (face form) */
+    GH_DUMP_PC_COEF = 24    /* float64 [n][dim] coefficient of each entry: sign (edge form), path edge vector (face form) */
 } gh_dump_item;
 
 gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *count, int32_t *elem_bytes);

@@ -109,7 +109,10 @@ bool is_device_ptr(const void *p) {
 void free_ws(Ctx *c, QueryWs *w) {
     DBuf *all[] = {&w->level, &w->parent, &w->pedge, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->twid, &w->gent,
                    &w->diag, &w->tiles, &w->ptile, &w->U0, &w->U1, &w->h, &w->g0, &w->g1, &w->l0, &w->l1, &w->z,
-                   &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1, &w->actl};
+                   &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1, &w->actl,
+                   &w->pc_src, &w->pc_lv, &w->pc_off, &w->pc_var, &w->pc_coef, &w->pc_entu, &w->pc_uvar,
+                   &w->pc_ucoef, &w->pc_dinv, &w->pc_L, &w->pc_drop, &w->pc_meta, &w->pc_val, &w->pc_delta,
+                   &w->pc_map};
     for (DBuf *b : all) dfree(c, *b);
 }
 
@@ -158,15 +161,22 @@ gh_status validate_params(const gh_params *p) {
         set_error("eps1 and eps2 must be finite and >= 0");
         return GH_EINVAL;
     }
+    if (p->path_constraints != 0 && p->path_constraints != 1) {
+        set_error("path_constraints must be 0 or 1");
+        return GH_EINVAL;
+    }
     return GH_OK;
 }
 
 // bytes one query's workspace needs
-size_t ws_bytes(const DevMesh &m, int fp64, int form) {
+size_t ws_bytes(const DevMesh &m, int fp64, int form, int path_constraints) {
     const size_t es = fp64 ? 8 : 4, xs = fp64 ? 16 : 8;
     size_t nv = m.nv, nf = m.nf, ne = m.ne;
     size_t b = nv * (5 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) + es * 3 * nf;
     b += (form == GH_FORM_FACE) ? es * 24 * nf : es * (9 * nf + 2 * ne);
+    // path constraints: the block's variable map and an allowance for the entries
+    // (sources x sets; their allocations are checked against the budget anyway)
+    if (path_constraints) b += 4 * ((form == GH_FORM_FACE) ? nf : ne) + (size_t)(kMaxPc + 1) * 64 * 1024;
     return b + (1 << 20);
 }
 
@@ -194,6 +204,7 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
     for (auto &e : ev) GH_CUDA(cudaEventCreate(&e));
     do {
         cudaEventRecord(ev[0], c->stream);
+        if ((s = build_path_constraints(c, items)) != GH_OK) break;
         if ((s = run_bfs(c, meshes, ws, srcs)) != GH_OK) break;
         for (int q = 0; q < K && s == GH_OK; ++q) {
             const gh_params *p = items[q].p;
@@ -242,7 +253,7 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
 gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
                      const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k) {
     const int K = (int)src.size();
-    size_t per = ws_bytes(m, p->fp64, p->form);
+    size_t per = ws_bytes(m, p->fp64, p->form, p->path_constraints);
     size_t avail;
     if (c->shared->budget) {
         size_t used = c->shared->in_use.load();
@@ -283,6 +294,14 @@ static gh_status solve_impl(gh_mesh_s *mh, const std::vector<std::vector<int32_t
         mh->h.gs_kernel_ms = ms6[5];
     }
     return s;
+}
+
+gh_status check_pc_sources(const gh_params *p, const std::vector<int32_t> &set) {
+    if (p->path_constraints && (int)set.size() > kMaxPc + 1) {
+        set_error("path_constraints takes at most " + std::to_string(kMaxPc + 1) + " sources");
+        return GH_EINVAL;
+    }
+    return GH_OK;
 }
 
 // sources of one set, validated, sorted and de-duplicated
@@ -361,6 +380,7 @@ void gh_params_default(gh_params *p) {
     p->early_stop = 0;
     p->eps1 = 1e-5;
     p->eps2 = 1e-5;
+    p->path_constraints = 0;
 }
 
 const char *gh_version(void) { return "geoheat 0.1 (sm_103a)"; }
@@ -526,6 +546,7 @@ gh_status gh_solve(gh_mesh mesh, const int32_t *src, int32_t nsrc, const gh_para
     GH_CUDA(cudaSetDevice(mesh->ctx->c.device));
     std::vector<std::vector<int32_t>> sets(1);
     if ((s = prep_sources(src, nsrc, mesh->h.m.nv, sets[0])) != GH_OK) return s;
+    if ((s = check_pc_sources(params, sets[0])) != GH_OK) return s;
     return solve_to(mesh, sets, params, d_out);
 }
 
@@ -541,6 +562,7 @@ gh_status gh_solve_batch(gh_mesh mesh, const int32_t *src_off, const int32_t *sr
         int32_t b = src_off[q], e = src_off[q + 1];
         if (b < 0 || e <= b) { set_error("src_off must be increasing and start at >= 0"); return GH_EINVAL; }
         if ((s = prep_sources(src + b, e - b, mesh->h.m.nv, sets[q])) != GH_OK) return s;
+        if ((s = check_pc_sources(params, sets[q])) != GH_OK) return s;
     }
     return solve_to(mesh, sets, params, d_out);
 }
@@ -580,6 +602,9 @@ gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *coun
         n = 1; eb = 8; break;
     case GH_DUMP_T: n = 1; eb = 8; break;
     case GH_DUMP_ITERS: n = 1; eb = 4; break;
+    case GH_DUMP_PC_OFF: n = w->pc_n ? w->pc_n + 1 : 0; break;
+    case GH_DUMP_PC_VAR: n = w->pc_ent; break;
+    case GH_DUMP_PC_COEF: n = (int64_t)w->pc_ent * w->pc_dim; eb = 8; break;
     default: set_error("unknown dump item"); return GH_EINVAL;
     }
     *count = n;
@@ -662,6 +687,9 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out) {
     case GH_DUMP_ITERS:
         GH_CUDA(cudaMemcpy(out, (const char *)w->actl.p + offsetof(AdmmCtl, iters_done), 4, cudaMemcpyDeviceToHost));
         return GH_OK;
+    case GH_DUMP_PC_OFF: return n ? cp(w->pc_off, 4 * n) : GH_OK;
+    case GH_DUMP_PC_VAR: return n ? cp(w->pc_var, 4 * n) : GH_OK;
+    case GH_DUMP_PC_COEF: return n ? cp(w->pc_coef, 8 * n) : GH_OK;
     default: set_error("unknown dump item"); return GH_EINVAL;
     }
 }

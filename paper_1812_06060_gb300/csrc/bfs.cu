@@ -582,10 +582,15 @@ static gh_status run_bfs_once(Ctx *c, std::vector<DevMesh *> &mq, std::vector<Qu
     return GH_OK;
 }
 
+gh_status run_bfs_fixed(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
+                        const std::vector<std::vector<int32_t>> &src, int cl) {
+    return run_bfs_once(c, mq, ws, src, cl);
+}
+
 // The breadth-first sets of every query.  The cluster size is tuned per mesh,
 // separately for single queries and batches: the first solve of each kind
-// runs every size the device supports once, timed with events, and keeps
-// the fastest (all sizes give the same sets and order, so the last run's
+// runs every size the device supports twice (alternating), timed with
+// events, and keeps the fastest (all sizes give the same sets and order, so the last run's
 // result is the solve's).  A batch over several meshes uses clusters of 8.
 gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
                   const std::vector<std::vector<int32_t>> &src) {

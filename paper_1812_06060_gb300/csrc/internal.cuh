@@ -182,6 +182,12 @@ struct QueryWs {
     DBuf resid;     // double [iters*2]
     DBuf actl;      // AdmmCtl: early termination of the ADMM
     DBuf e1;        // double [1]
+    // multi-source path constraints (Sec. 5.2), built per solve when asked for
+    // (see paths.cu): entries, distinct variables, Gram factor, per-iteration
+    // values and corrections, and the block's variable -> distinct index map
+    DBuf pc_src, pc_lv, pc_off, pc_var, pc_coef, pc_entu, pc_uvar, pc_ucoef, pc_dinv, pc_L, pc_drop, pc_meta;
+    DBuf pc_val, pc_delta, pc_map;
+    int pc_n = 0, pc_ent = 0, pc_dim = 1;   // constraints and entries of the last solve (0: none)
     // host-side facts of the last run
     int nlev = 0, nreach = 0, final_buf = 0, form = 1, admm_iters = 0, diagnostics = 0, sweeps = 0;
     double t = 0.0;
@@ -212,10 +218,12 @@ struct Item {
     double *d_out_dev;                 // device, [m->nv] (may be null)
 };
 gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6);
-size_t ws_bytes(const DevMesh &m, int fp64, int form);
+size_t ws_bytes(const DevMesh &m, int fp64, int form, int path_constraints);
 void free_ws(Ctx *c, QueryWs *w);
 gh_status validate_params(const gh_params *p);
 gh_status prep_sources(const int32_t *src, int32_t nsrc, int64_t nv, std::vector<int32_t> &out);
+constexpr int kMaxPc = 31;   // path constraints per query: sources - 1 (one warp per constraint)
+gh_status check_pc_sources(const gh_params *p, const std::vector<int32_t> &set);
 bool is_device_ptr(const void *p);
 
 // ---------------------------------------------------------------- kernels (host launchers)
@@ -233,6 +241,9 @@ gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_d
 // breadth-first sets of every query (each on its own mesh) in one launch
 gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
                   const std::vector<std::vector<int32_t>> &src);
+// the same with a given cluster size (8 is always supported), no tuning
+gh_status run_bfs_fixed(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
+                        const std::vector<std::vector<int32_t>> &src, int cl);
 bool bfs_cluster_supported(int cl);
 gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
 
@@ -241,6 +252,11 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
 // one persistent diffusion launch for all queries (each with its own sweeps,
 // in QueryWs::sweeps; all of one precision)
 gh_status run_gs(Ctx *c, std::vector<QueryWs *> &ws, cudaEvent_t ev0, cudaEvent_t ev1);
+
+// paths.cu
+// the multi-source path constraints of every item that asks for them; runs
+// before the items' own traversal (it uses their traversal buffers)
+gh_status build_path_constraints(Ctx *c, std::vector<Item> &items);
 
 // stages.cu
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q);

@@ -113,7 +113,7 @@ static void worker_loop(Engine *E, Worker *W) {
                 std::vector<QueryWs *> &pool = W->pools[m];
                 const size_t k = taken[m];
                 const bool reuse = k < pool.size() && pool[k]->level.p;
-                const size_t cost = reuse ? 0 : ws_bytes(*m, fp64, r->p.form);
+                const size_t cost = reuse ? 0 : ws_bytes(*m, fp64, r->p.form, r->p.path_constraints);
                 if (!batch.empty() && cost > avail) break;   // the rest waits for memory
                 avail -= std::min(cost, avail);
                 if (k == pool.size()) pool.push_back(new QueryWs());
@@ -256,7 +256,8 @@ gh_status gh_submit(gh_ctx ctx, gh_mesh mesh, const int32_t *src, int32_t nsrc, 
     if (s != GH_OK) return s;
     auto *r = new Request();
     cudaSetDevice(gh_ctx_launcher(ctx)->device);
-    if ((s = prep_sources(src, nsrc, gh_mesh_host(mesh)->m.nv, r->src)) != GH_OK) {
+    if ((s = prep_sources(src, nsrc, gh_mesh_host(mesh)->m.nv, r->src)) != GH_OK ||
+        (s = check_pc_sources(params, r->src)) != GH_OK) {
         delete r;
         return s;
     }

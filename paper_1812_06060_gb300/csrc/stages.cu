@@ -2,6 +2,7 @@
 // eq. HeatDiffusionNormalization), the face-based ADMM (Sec. 3.2), the
 // edge-based ADMM (Sec. 4.1), breadth-first integration (eq. IntegrationStep,
 // Sec. 4) and the heat residual E1 (eq. HeatSolutionError).
+#include "admm.cuh"
 #include "internal.cuh"
 
 namespace gh {
@@ -189,69 +190,45 @@ __global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32
     o[13] = o[14] = o[15] = T(0);
 }
 
-// four values loaded as one vector (16 bytes in FP32, 32 in FP64)
-template <class T> struct alignas(4 * sizeof(T)) Quad { T x, y, z, w; };
-
 // One ADMM iteration per face, Y then G then lambda (Sec. 3.2), with the
 // multiplier of slot k carried as q_k = g - lambda_k/(mu alpha) (the Y
-// subproblem's input; lambda_k/(mu alpha) = g - q_k):
-//   y_k = q_k + A'/(A + A') ebar (ebar . (q'_k - q_k))   (q' of the twin slot)
-//   g'  = (2h + mu sum_k (y_k + g - q_k)) / (2 + mu n)
+// subproblem's input; lambda_k/(mu alpha) = g - q_k): face_update gives the
+// Y- and G-updates, then
 //   lambda_k += mu alpha (y_k - g')  <=>  q_k' = 2g' - g + q_k - y_k
-// over the n interior slots; the twins' q are the previous iteration's
-// (buffers *_in), the new g and q go to *_out.
+// over the interior slots; the twins' q are the previous iteration's
+// (buffers *_in), the new g and q go to *_out.  With multi-source path
+// constraints, g' = gn - delta on the constrained faces (pcm[f] = the face's
+// index in delta, else -1), the correction of the KKT projection.
 // Optional residual partials per block: [0] |alpha (y - g')|^2,
 // [1] |mu alpha (g' - g)|^2 summed over interior slots.
 template <class T>
 __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ twin,
                                                   const T *__restrict__ rec, const T *__restrict__ h,
                                                   const T *__restrict__ g_in, const T *__restrict__ q_in, T *g_out,
-                                                  T *q_out, T mu, double *part, const AdmmCtl *ctl, int first) {
+                                                  T *q_out, T mu, double *part, const AdmmCtl *ctl, int first,
+                                                  const int32_t *__restrict__ pcm, const T *__restrict__ pcd) {
     if (ctl && ctl->stop) return;   // the residuals met the thresholds (the same for every thread)
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
     if (f < nf) {
-        const Quad<T> *r4 = reinterpret_cast<const Quad<T> *>(rec + 16 * f);
-        const Quad<T> ek[3] = {r4[0], r4[1], r4[2]};
-        const T alpha = r4[3].x;
-        T g[3], q[3][3], y[3][3];
-        bool in[3];
-        // the first iteration starts from g = h and q_k = h on every slot (lambda = 0)
-        const T *gsrc = first ? h : g_in;
-        for (int c = 0; c < 3; ++c) g[c] = gsrc[3 * f + c];
-        T acc[3] = {0, 0, 0};
-        int n = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            for (int c = 0; c < 3; ++c) q[k][c] = first ? g[c] : q_in[9 * f + 3 * k + c];
-            const int tw = twin[3 * f + k];
-            in[k] = tw >= 0;
-            if (!in[k]) continue;
-            const T *qt = first ? h + 3 * (int64_t)(tw >> 2) : q_in + 9 * (int64_t)(tw >> 2) + 3 * (tw & 3);
-            const T eb[3] = {ek[k].x, ek[k].y, ek[k].z};
-            const T proj = eb[0] * (qt[0] - q[k][0]) + eb[1] * (qt[1] - q[k][1]) + eb[2] * (qt[2] - q[k][2]);
-            for (int c = 0; c < 3; ++c) {
-                y[k][c] = q[k][c] + ek[k].w * eb[c] * proj;
-                acc[c] += y[k][c] + (g[c] - q[k][c]);
-            }
-            ++n;
+        FaceIter<T> s;
+        face_update(f, twin, rec, h, g_in, q_in, mu, first, s);
+        if (pcm) {
+            const int u = pcm[f];
+            if (u >= 0)
+                for (int c = 0; c < 3; ++c) s.gn[c] -= pcd[3 * u + c];
         }
-        T gn[3];
-        const T den = T(2) + mu * T(n);
-        for (int c = 0; c < 3; ++c) {
-            gn[c] = (T(2) * h[3 * f + c] + mu * acc[c]) / den;
-            g_out[3 * f + c] = gn[c];
-        }
+        for (int c = 0; c < 3; ++c) g_out[3 * f + c] = s.gn[c];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             for (int c = 0; c < 3; ++c) {
-                T qn = gn[c];
-                if (in[k]) {
-                    qn = T(2) * gn[c] - g[c] + q[k][c] - y[k][c];
+                T qn = s.gn[c];
+                if (s.in[k]) {
+                    qn = T(2) * s.gn[c] - s.g[c] + s.q[k][c] - s.y[k][c];
                     if (part) {   // residual norms only when asked for (FP64 arithmetic is slow here)
-                        const T r = alpha * (y[k][c] - gn[c]);
+                        const T r = s.alpha * (s.y[k][c] - s.gn[c]);
                         rp += (double)r * (double)r;
-                        const double dgv = (double)mu * (double)alpha * ((double)gn[c] - (double)g[c]);
+                        const double dgv = (double)mu * (double)s.alpha * ((double)s.gn[c] - (double)s.g[c]);
                         rd += dgv * dgv;
                     }
                 }
@@ -331,32 +308,31 @@ __global__ void k_edge_face_pass(int64_t nf, const int32_t *__restrict__ face_ed
     for (int k = 0; k < 3; ++k) w[3 * f + k] = v[k] - q[k] * qv / T(3);
 }
 
-// X-update (eq. xeupdate): x_e = (sum z + sum (lambda + mu w)) / (n_e (1 + mu));
-// optional residual partials per block: [0] sum (w - x)^2, [1] sum (mu dx)^2
-// over the edge's slots
+// X-update (eq. xeupdate, edge_update); with multi-source path constraints
+// x = x_hat - delta on the constrained edges (pcm[e] = the edge's index in
+// delta, else -1).  Optional residual partials per block: [0] sum (w - x)^2,
+// [1] sum (mu dx)^2 over the edge's slots
 template <class T>
 __global__ void __launch_bounds__(NT) k_edge_edge_pass(int64_t ne, const int32_t *__restrict__ edge_face,
                                                        const int32_t *__restrict__ edge_slot, const T *__restrict__ sz,
                                                        const T *__restrict__ w, const T *__restrict__ lam, T *x, T mu,
-                                                       double *part, const AdmmCtl *ctl) {
+                                                       double *part, const AdmmCtl *ctl,
+                                                       const int32_t *__restrict__ pcm, const T *__restrict__ pcd) {
     if (ctl && ctl->stop) return;
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
     if (e < ne) {
-        T s = sz[e];
-        int n = 0;
         int sl[2];
-        for (int j = 0; j < 2; ++j) {
-            int f = edge_face[2 * e + j];
-            sl[j] = -1;
-            if (f >= 0) {
-                sl[j] = 3 * f + edge_slot[2 * e + j];
-                s += lam[sl[j]] + mu * w[sl[j]];
-                ++n;
-            }
+        // x[e] is read before the update on purpose: with the read issued
+        // only for the residuals, the kernel wrote x without reading it and
+        // ran 6x slower on GB300 (its L2 compression counters show every
+        // written sector of x going through the compressor)
+        const T xo = x[e];
+        T xn = edge_update(e, edge_face, edge_slot, sz, w, lam, mu, sl);
+        if (pcm) {
+            const int u = pcm[e];
+            if (u >= 0) xn -= pcd[u];
         }
-        T xo = x[e];
-        T xn = s / (T(n) * (T(1) + mu));
         x[e] = xn;
         if (part) {
             for (int j = 0; j < 2; ++j) {
@@ -399,6 +375,80 @@ __global__ void k_resid_final(const double *__restrict__ part, int nblocks, doub
         __syncthreads();
     }
     if (threadIdx.x == 0) { out[0] = sqrt(s0[0]); out[1] = sqrt(s1[0]); }
+}
+
+// ------------------------------------------------------------------ path constraints
+
+// Per ADMM iteration, before the block update: the KKT projection of the
+// multi-source path constraints (Sec. 5.2) on the constrained variables.
+// One CTA: vhat of every constrained variable (face_update / edge_update,
+// the update kernel's own code), r_j = sum over constraint j's entries of
+// c . vhat (one warp per constraint, fixed order), nu from the Gram factor,
+// then delta_u = (1/D_u) sum_j c_uj nu_j, which the update kernel subtracts.
+constexpr int PJ = 1024;
+
+template <class T>
+__device__ void pc_finish(const PcDev &pc, const T *val, T *delta) {
+    __shared__ double s_r[kMaxPc], s_nu[kMaxPc];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, dim = pc.dim, npc = pc.npc;
+    if (warp < npc) {
+        double acc = 0.0;
+        for (int i = pc.off[warp] + lane; i < pc.off[warp + 1]; i += 32) {
+            const int u = pc.entu[i];
+            for (int c = 0; c < dim; ++c) acc += pc.coef[(size_t)i * dim + c] * (double)val[(size_t)u * dim + c];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_r[warp] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) pc_solve(pc.L, pc.drop, npc, s_r, s_nu);
+    __syncthreads();
+    const int nu = pc.meta[0];
+    for (int u = tid; u < nu; u += PJ)
+        for (int c = 0; c < dim; ++c) {
+            double sum = 0.0;
+            for (int j = 0; j < npc; ++j) sum += pc.ucoef[((size_t)u * npc + j) * dim + c] * s_nu[j];
+            delta[(size_t)u * dim + c] = (T)(pc.dinv[u] * sum);
+        }
+}
+
+template <class T>
+__global__ void __launch_bounds__(PJ, 1) k_pc_project_face(PcDev pc, const int32_t *__restrict__ twin,
+                                                        const T *__restrict__ rec, const T *__restrict__ h,
+                                                        const T *__restrict__ g_in, const T *__restrict__ q_in, T mu,
+                                                        int first, T *val, T *delta, const AdmmCtl *ctl) {
+    if (ctl && ctl->stop) return;
+    const int nu = pc.meta[0];
+    for (int u = threadIdx.x; u < nu; u += PJ) {
+        FaceIter<T> s;
+        face_update((int64_t)pc.uvar[u], twin, rec, h, g_in, q_in, mu, first, s);
+        for (int c = 0; c < 3; ++c) val[3 * u + c] = s.gn[c];
+    }
+    __syncthreads();
+    pc_finish(pc, val, delta);
+}
+
+template <class T>
+__global__ void __launch_bounds__(PJ, 1) k_pc_project_edge(PcDev pc, const int32_t *__restrict__ edge_face,
+                                                        const int32_t *__restrict__ edge_slot,
+                                                        const T *__restrict__ sz, const T *__restrict__ w,
+                                                        const T *__restrict__ lam, T mu, T *val, T *delta,
+                                                        const AdmmCtl *ctl) {
+    if (ctl && ctl->stop) return;
+    const int nu = pc.meta[0];
+    for (int u = threadIdx.x; u < nu; u += PJ) {
+        int sl[2];
+        val[u] = edge_update((int64_t)pc.uvar[u], edge_face, edge_slot, sz, w, lam, mu, sl);
+    }
+    __syncthreads();
+    pc_finish(pc, val, delta);
+}
+
+PcDev pc_dev(const QueryWs &q) {
+    return PcDev{q.pc_n, q.pc_dim, q.pc_ent, ptr<int32_t>(q.pc_off), ptr<int32_t>(q.pc_var),
+                 ptr<int32_t>(q.pc_entu), ptr<int32_t>(q.pc_uvar), ptr<int32_t>(q.pc_meta), ptr<int32_t>(q.pc_drop),
+                 ptr<double>(q.pc_coef), ptr<double>(q.pc_ucoef), ptr<double>(q.pc_dinv), ptr<double>(q.pc_L)};
 }
 
 // ------------------------------------------------------------------ integration
@@ -547,10 +597,18 @@ template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int ite
         k_face_mnorm2<<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), ptr<double>(m.Af), part); ++c->launches;
         k_ctl_thresholds<<<1, NT, 0, st>>>(part, (int)nb, eps1, eps2, ctl); ++c->launches;
     }
+    const bool pc = q.pc_n > 0;
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;
+        if (pc) {
+            k_pc_project_face<T><<<1, PJ, 0, st>>>(pc_dev(q), ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a],
+                                                  (T)mu, it == 0, ptr<T>(q.pc_val), ptr<T>(q.pc_delta),
+                                                  early ? ctl : nullptr); ++c->launches;
+        }
         k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1],
-                                          qq[a ^ 1], (T)mu, part, early ? ctl : nullptr, it == 0); ++c->launches;
+                                          qq[a ^ 1], (T)mu, part, early ? ctl : nullptr, it == 0,
+                                          pc ? ptr<int32_t>(q.pc_map) : nullptr, pc ? ptr<T>(q.pc_delta) : nullptr);
+        ++c->launches;
         if (part) {
             k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it, early ? ctl : nullptr); ++c->launches;
         }
@@ -583,11 +641,19 @@ template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, i
         k_ctl_thresholds<<<1, NT, 0, st>>>(part, (int)nbz, eps1, eps2, ctl); ++c->launches;
     }
     const AdmmCtl *cx = early ? ctl : nullptr;
+    const bool pc = q.pc_n > 0;
     for (int it = 0; it < iters; ++it) {
         k_edge_face_pass<T><<<nbf, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), ptr<int8_t>(m.face_sign),
                                                 ptr<T>(q.x), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, it > 0, cx); ++c->launches;
+        if (pc) {
+            k_pc_project_edge<T><<<1, PJ, 0, st>>>(pc_dev(q), ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
+                                                  ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, ptr<T>(q.pc_val),
+                                                  ptr<T>(q.pc_delta), cx); ++c->launches;
+        }
         k_edge_edge_pass<T><<<nbe, NT, 0, st>>>(m.ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
-                                                ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x), (T)mu, part, cx); ++c->launches;
+                                                ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x), (T)mu, part, cx,
+                                                pc ? ptr<int32_t>(q.pc_map) : nullptr,
+                                                pc ? ptr<T>(q.pc_delta) : nullptr); ++c->launches;
         if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nbe, ptr<double>(q.resid) + 2 * it, cx); ++c->launches; }
         if (early) { k_admm_check<<<1, 1, 0, st>>>(ptr<double>(q.resid) + 2 * it, ctl, it); ++c->launches; }
     }

@@ -48,3 +48,29 @@ def test_missing_library_fails_loudly(tmp_path):
             g.load_library(str(tmp_path / "nope.so"))
         finally:
             g._lib = saved
+
+
+def _header_text():
+    return open(os.path.join(ROOT, "include", "geoheat.h")).read()
+
+
+def test_params_struct_matches_header():
+    import paper_1812_06060_gb300 as g
+    body = re.search(r"typedef struct \{(.*?)\} gh_params;", _header_text(), re.S).group(1)
+    fields = re.findall(r"\b(\w+);", re.sub(r"/\*.*?\*/", "", body, flags=re.S))
+    assert [f[0] for f in g.GhParams._fields_] == fields
+
+
+def test_dump_items_match_header():
+    import paper_1812_06060_gb300 as g
+    items = re.findall(r"\b(GH_DUMP_\w+) = (\d+)", _header_text())
+    assert len(items) >= 25
+    for name, val in items:
+        assert getattr(g, name) == int(val), name
+
+
+def test_params_defaults_and_path_constraints_flag(libpath):
+    import paper_1812_06060_gb300 as g
+    g.load_library(libpath)
+    assert g.params().path_constraints == 0
+    assert g.params(path_constraints=True).path_constraints == 1
