@@ -262,6 +262,36 @@ def jittered_grid(N: int, seed: int | None, jitter: float = 0.2) -> Mesh:
     return Mesh(V=V, F=F, name=f"grid{N}", meta={"N": N, "seed": seed, "jitter": jitter})
 
 
+def torus(nu: int, nw: int, seed: int | None = None, R: float = 1.0, r: float = 0.4, jitter: float = 0.2) -> Mesh:
+    """Closed torus of genus 1: vertex (i, j) = index i*nw + j at major angle
+    a = 2 pi i / nu and minor angle b = 2 pi j / nw, p = ((R + r cos b) cos a,
+    (R + r cos b) sin a, r sin b).  Each cell (i, j)-(i+1, j+1) (indices
+    wrapping around) is split along one of its diagonals by the parity of
+    i + j, faces counter-clockwise seen from outside.  With a seed both
+    angles move by independent uniform offsets in [-jitter, jitter) of a
+    step."""
+    i, j = np.meshgrid(np.arange(nu), np.arange(nw), indexing="ij")
+    a = 2.0 * np.pi * i.ravel() / nu
+    b = 2.0 * np.pi * j.ravel() / nw
+    if seed is not None and jitter > 0:
+        rng = rng_for(seed)
+        d = (rng.random((nu * nw, 2)) * 2.0 - 1.0) * jitter
+        a = a + d[:, 0] * (2.0 * np.pi / nu)
+        b = b + d[:, 1] * (2.0 * np.pi / nw)
+    V = np.stack([(R + r * np.cos(b)) * np.cos(a), (R + r * np.cos(b)) * np.sin(a), r * np.sin(b)], axis=1)
+    ci, cj = np.meshgrid(np.arange(nu), np.arange(nw), indexing="ij")
+    ci, cj = ci.ravel(), cj.ravel()
+    v00 = ci * nw + cj
+    v10 = ((ci + 1) % nu) * nw + cj
+    v01 = ci * nw + (cj + 1) % nw
+    v11 = ((ci + 1) % nu) * nw + (cj + 1) % nw
+    even = (ci + cj) % 2 == 0
+    t1 = np.where(even[:, None], np.stack([v00, v10, v11], 1), np.stack([v00, v10, v01], 1))
+    t2 = np.where(even[:, None], np.stack([v00, v11, v01], 1), np.stack([v10, v11, v01], 1))
+    F = np.stack([t1, t2], axis=1).reshape(-1, 3).astype(np.int32)
+    return Mesh(V=V, F=F, name=f"torus{nu}x{nw}", meta={"nu": nu, "nw": nw, "seed": seed})
+
+
 def strip_grid(nx: int, ny: int) -> Mesh:
     """Regular ny x nx vertex grid with unit spacing (vertex (i, j) = index
     i*nx + j at (x, y) = (j, i)), cells split by the same alternating

@@ -349,6 +349,173 @@ def path_constraints(md: MeshData, sources, form: str) -> PathConstraints:
                            np.asarray(coef, np.float64).reshape(-1, dim), paths)
 
 
+def _bfs_graph(rowptr, col, sources):
+    """orc_bfs on any graph in CSR form (rows ascending): set index and FIFO
+    pairing node of every node."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col if len(col) else np.zeros(1), dtype=np.int32)
+    n = len(rowptr) - 1
+    src = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)
+    level = np.empty(n, np.int32)
+    parent = np.empty(n, np.int32)
+    order = np.full(n, -1, np.int32)
+    level_off = np.empty(n + 1, np.int32)
+    _check(lib().orc_bfs(n, _p(rowptr), _p(col), src.size, _p(src), _p(level), _p(parent), _p(order),
+                         _p(level_off)), "orc_bfs")
+    return level, parent
+
+
+def _csr(rows):
+    """rows: list of lists of (node, edge) -> rowptr, col, col_edge, each row
+    sorted by node"""
+    rowptr = [0]
+    col, cedge = [], []
+    for r in rows:
+        for nb, e in sorted(r):
+            col.append(nb)
+            cedge.append(e)
+        rowptr.append(len(col))
+    return np.asarray(rowptr, np.int32), np.asarray(col, np.int32), np.asarray(cedge, np.int32)
+
+
+def _tree_edges(rowptr, col_edge, col, level, parent):
+    """edge crossed from each node to its pairing node"""
+    pe = np.full(len(level), -1, np.int64)
+    for v in range(len(level)):
+        if level[v] > 0:
+            for j in range(rowptr[v], rowptr[v + 1]):
+                if col[j] == parent[v]:
+                    pe[v] = col_edge[j]
+                    break
+    return pe
+
+
+def _lca_walk(a, b, level, parent):
+    """the tree paths a -> lca and b -> lca (node lists, lca last)"""
+    pa, pb = [a], [b]
+    while level[pa[-1]] > level[pb[-1]]:
+        pa.append(int(parent[pa[-1]]))
+    while level[pb[-1]] > level[pa[-1]]:
+        pb.append(int(parent[pb[-1]]))
+    while pa[-1] != pb[-1]:
+        pa.append(int(parent[pa[-1]]))
+        pb.append(int(parent[pb[-1]]))
+    return pa, pb
+
+
+def cycle_constraints(md: MeshData, form: str) -> PathConstraints:
+    """Integrability on a cycle basis (Sec. 5.1, eq. TopologyConstraint,
+    eq. EdgeTopologyConstraint) from a tree-cotree decomposition.
+
+    READING: the paper treats surfaces of genus g (2g non-contractible
+    cycles) and says nothing of boundaries; a mesh with boundary edges gets
+    no cycle constraints here.  The trees are breadth-first trees with FIFO
+    pairing (eq. VertexSets), rooted at vertex 0 and face 0, rows in
+    ascending order:
+    edge form: T = the primal tree; C = the dual tree over the edges not in
+      T; each edge in neither closes the cycle e, then T from its higher
+      end to the common ancestor and back down to its lower end, oriented
+      lower end -> higher end first; coefficient +1 where the cycle runs
+      along the edge's orientation halfedge, -1 against it;
+    face form: T* = the dual tree (faces across edges); C = the primal tree
+      over the edges not crossed by T*; each edge in neither closes a loop of
+      faces: its lower face, its higher face, then T* up to the common
+      ancestor and back down; for every face of the loop the coefficient is
+      the segment between the midpoints of the edge it is entered through
+      and the edge it is left through.
+    Cycles come in ascending order of their closing edge."""
+    nv, nf, ne = md.nv, md.nf, md.ne
+    empty = PathConstraints(np.zeros(1, np.int32), np.zeros(0, np.int32),
+                            np.zeros((0, 1 if form == "edge" else 3)), [])
+    if (md.edge_face[:, 1] < 0).any() or nf == 0:
+        return empty
+    efaces = md.edge_face
+    dual_all = [[] for _ in range(nf)]
+    for e in range(ne):
+        f1, f2 = int(efaces[e, 0]), int(efaces[e, 1])
+        dual_all[f1].append((f2, e))
+        dual_all[f2].append((f1, e))
+    off, var, coef, cycles = [0], [], [], []
+    if form == "edge":
+        plev, ppar = _bfs_graph(md.rowptr, md.col, [0])
+        pedge = _tree_edges(md.rowptr, md.col_edge, md.col, plev, ppar)
+        tree = np.zeros(ne, bool)
+        tree[pedge[pedge >= 0]] = True
+        drp, dcol, dce = _csr([[x for x in r if not tree[x[1]]] for r in dual_all])
+        dlev, dpar = _bfs_graph(drp, dcol, [0])
+        dedge = _tree_edges(drp, dce, dcol, dlev, dpar)
+        dual = np.zeros(ne, bool)
+        dual[dedge[dedge >= 0]] = True
+        for e in np.flatnonzero(~tree & ~dual):
+            a, b = int(md.edges[e, 0]), int(md.edges[e, 1])
+            pa, pb = _lca_walk(a, b, plev, ppar)
+            nodes = [a] + pb + pa[::-1][1:]          # a -> b -> ... -> lca -> ... -> a
+            steps = list(zip(nodes[:-1], nodes[1:]))
+            for p, q in steps:
+                ee = _edge_id(md, p, q)
+                x, y = int(md.edges[ee, 0]), int(md.edges[ee, 1])
+                tail = y if (md.flip is not None and md.flip[ee]) else x
+                var.append(ee)
+                coef.append([1.0 if p == tail else -1.0])
+            off.append(len(var))
+            cycles.append(steps)
+    elif form == "face":
+        drp, dcol, dce = _csr(dual_all)
+        dlev, dpar = _bfs_graph(drp, dcol, [0])
+        dedge = _tree_edges(drp, dce, dcol, dlev, dpar)
+        dual = np.zeros(ne, bool)
+        dual[dedge[dedge >= 0]] = True
+        keep = ~dual[md.col_edge]
+        rows = [[(int(md.col[j]), int(md.col_edge[j])) for j in range(md.rowptr[v], md.rowptr[v + 1]) if keep[j]]
+                for v in range(nv)]
+        crp, ccol, cce = _csr(rows)
+        clev, cpar = _bfs_graph(crp, ccol, [0])
+        cedge = _tree_edges(crp, cce, ccol, clev, cpar)
+        cot = np.zeros(ne, bool)
+        cot[cedge[cedge >= 0]] = True
+        mid = 0.5 * (md.P[md.edges[:, 0]] + md.P[md.edges[:, 1]])
+
+        def crossing(f, g):
+            for nb, e in dual_all[f]:
+                if nb == g:
+                    return e
+            raise ValueError("faces not adjacent")
+
+        for e in np.flatnonzero(~dual & ~cot):
+            f1, f2 = int(efaces[e, 0]), int(efaces[e, 1])
+            pa, pb = _lca_walk(f1, f2, dlev, dpar)
+            loop = [f1] + pb + pa[::-1][1:]         # f1 -> f2 -> ... -> lca -> ... -> f1
+            cross = [crossing(x, y) for x, y in zip(loop[:-1], loop[1:])]
+            m = len(cross)
+            for i in range(m):                        # face loop[i] entered via cross[i-1], left via cross[i]
+                var.append(loop[i])
+                coef.append(list(mid[cross[i]] - mid[cross[i - 1]]))
+            off.append(len(var))
+            cycles.append(loop)
+    else:
+        raise ValueError(form)
+    dim = 1 if form == "edge" else 3
+    return PathConstraints(np.asarray(off, np.int32), np.asarray(var, np.int32),
+                           np.asarray(coef, np.float64).reshape(-1, dim), cycles)
+
+
+def join_constraints(*pcs) -> PathConstraints:
+    """One constraint list from several, in the given order."""
+    pcs = [p for p in pcs if p is not None]
+    off = [0]
+    var, coef, paths = [], [], []
+    for p in pcs:
+        base = off[-1]
+        off.extend(base + int(x) for x in p.off[1:])
+        var.append(p.var)
+        coef.append(p.coef)
+        paths.extend(p.paths)
+    dim = pcs[0].coef.shape[1] if pcs else 1
+    return PathConstraints(np.asarray(off, np.int32),
+                           np.concatenate(var).astype(np.int32) if var else np.zeros(0, np.int32),
+                           np.concatenate(coef) if coef else np.zeros((0, dim)), paths)
+
+
 def _pc_args(pc, dim):
     if pc is None or len(pc.off) < 2:
         z = np.zeros(1, np.int32)
@@ -390,18 +557,26 @@ def diffusion_time(md: MeshData, m: float = 1.0) -> float:
 
 
 def solve(md: MeshData, sources, form: str = "edge", sweeps: int = 200, m: float = 1.0, t: float | None = None,
-          admm_iters: int = ADMM_ITERS, mu: float = MU, eps=None, path_constraints_on: bool = False) -> dict:
+          admm_iters: int = ADMM_ITERS, mu: float = MU, eps=None, path_constraints_on: bool = False,
+          cycle_constraints_on: bool = False) -> dict:
     """Algorithm 1 end to end: Diffusion -> normalise -> Integrable ->
     Recovery, in the face form (Sec. 3) or the edge form (Sec. 4).  Returns
     every intermediate.  eps = (eps1, eps2) ends the ADMM early on its
     residuals (Sec. 3.2); the iterations run are len(out["res"]).
-    path_constraints_on adds the multi-source constraints (Sec. 5.2)."""
+    path_constraints_on adds the multi-source constraints (Sec. 5.2),
+    cycle_constraints_on the cycle constraints of a closed mesh of genus
+    g >= 1 (Sec. 5.1), after the path constraints."""
     t = diffusion_time(md, m) if t is None else t
     b = bfs(md, sources)
     st = gs(md, b, t, sweeps)
     h = normalize(md, st)
     out = {"t": t, "bfs": b, "u": st, "h": h}
-    pc = path_constraints(md, sources, form) if path_constraints_on else None
+    parts = []
+    if path_constraints_on:
+        parts.append(path_constraints(md, sources, form))
+    if cycle_constraints_on:
+        parts.append(cycle_constraints(md, form))
+    pc = join_constraints(*parts) if parts else None
     if pc is not None:
         out["pc"] = pc
     if form == "face":

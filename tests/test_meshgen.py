@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import meshgen
+import oracle
 
 
 def _edges(F):
@@ -68,3 +69,18 @@ def test_sources():
 def test_workload_c1_shape():
     w = meshgen.workload_c1()
     assert w.mesh.nv == 2562 and w.mesh.nf == 5120 and list(w.sources[0]) == [0]
+
+
+def test_torus_is_closed_oriented_genus_one():
+    m = meshgen.torus(16, 10, seed=2)
+    md = oracle.mesh_data(m.V, m.F)          # rejects inconsistent orientation
+    assert md.nv == 160 and md.nf == 320 and md.ne == 480
+    assert (md.edge_face[:, 1] >= 0).all()
+    assert md.nv - md.ne + md.nf == 0
+    # outward normals: the face normal points away from the core circle
+    p = md.P[m.F].mean(1)
+    n = np.cross(md.P[m.F[:, 1]] - md.P[m.F[:, 0]], md.P[m.F[:, 2]] - md.P[m.F[:, 0]])
+    core = p.copy()
+    core[:, 2] = 0
+    core *= (1.0 / np.linalg.norm(core, axis=1))[:, None]
+    assert np.all(np.einsum("ij,ij->i", n, p - core) > 0)
