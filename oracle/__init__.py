@@ -408,8 +408,9 @@ def cycle_constraints(md: MeshData, form: str) -> PathConstraints:
     eq. EdgeTopologyConstraint) from a tree-cotree decomposition.
 
     READING: the paper treats surfaces of genus g (2g non-contractible
-    cycles) and says nothing of boundaries; a mesh with boundary edges gets
-    no cycle constraints here.  The trees are breadth-first trees with FIFO
+    cycles) and says nothing of boundaries; only a connected closed mesh
+    gets cycle constraints here (a mesh with boundary edges, or whose trees
+    below do not reach every vertex and face, gets none).  The trees are breadth-first trees with FIFO
     pairing (eq. VertexSets), rooted at vertex 0 and face 0, rows in
     ascending order:
     edge form: T = the primal tree; C = the dual tree over the edges not in
@@ -443,6 +444,8 @@ def cycle_constraints(md: MeshData, form: str) -> PathConstraints:
         tree[pedge[pedge >= 0]] = True
         drp, dcol, dce = _csr([[x for x in r if not tree[x[1]]] for r in dual_all])
         dlev, dpar = _bfs_graph(drp, dcol, [0])
+        if (plev < 0).any() or (dlev < 0).any():
+            return empty
         dedge = _tree_edges(drp, dce, dcol, dlev, dpar)
         dual = np.zeros(ne, bool)
         dual[dedge[dedge >= 0]] = True
@@ -470,6 +473,8 @@ def cycle_constraints(md: MeshData, form: str) -> PathConstraints:
                 for v in range(nv)]
         crp, ccol, cce = _csr(rows)
         clev, cpar = _bfs_graph(crp, ccol, [0])
+        if (dlev < 0).any() or (clev < 0).any():
+            return empty
         cedge = _tree_edges(crp, cce, ccol, clev, cpar)
         cot = np.zeros(ne, bool)
         cot[cedge[cedge >= 0]] = True

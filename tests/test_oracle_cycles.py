@@ -139,3 +139,12 @@ def test_cycle_constraints_hold_and_are_the_kkt_minimiser(torus, form):
     assert np.abs(vc - vh).max() > 1e-6
     assert np.abs(vc - sol).max() <= 1e-12 * max(1.0, np.abs(vh).max())
     assert np.abs(S @ v10).max() <= 1e-12 * np.abs(v10).max() * np.abs(S).sum(1).max()
+
+
+@pytest.mark.parametrize("form", ["edge", "face"])
+def test_disconnected_closed_mesh_gets_none(form):
+    a = meshgen.torus(12, 8, seed=1)
+    V = np.vstack([a.V, a.V + [5.0, 0.0, 0.0]])
+    F = np.vstack([a.F, a.F + a.V.shape[0]])
+    md = oracle.mesh_data(V, F)
+    assert len(oracle.cycle_constraints(md, form).off) == 1
