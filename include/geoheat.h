@@ -89,6 +89,15 @@ typedef enum { GH_FORM_FACE = 0, GH_FORM_EDGE = 1 } gh_form;
  *              update, whose minimiser under them is a projection through a
  *              small Gram system.  At most 32 sources (GH_EINVAL otherwise).
  *              No effect with one source.  Default 0.
+ *  cycle_constraints  1: on a connected closed mesh of genus g >= 1, also
+ *              make the line integral vanish around each of the 2g cycles of
+ *              a tree-cotree basis (Sec. 5.1, eq. TopologyConstraint,
+ *              eq. EdgeTopologyConstraint): cycles of edges in the edge form,
+ *              loops of faces through edge midpoints in the face form, built
+ *              once per mesh and form from breadth-first trees rooted at
+ *              vertex 0 and face 0.  A mesh with boundary edges or in several
+ *              pieces gets none.  Path and cycle constraints together: at
+ *              most 31 (GH_EINVAL otherwise).  Default 0.
  */
 typedef struct {
     double m;
@@ -103,6 +112,7 @@ typedef struct {
     double eps1;
     double eps2;
     int32_t path_constraints;
+    int32_t cycle_constraints;
 } gh_params;
 
 /* Fills *p with the defaults listed above. */

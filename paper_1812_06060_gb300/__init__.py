@@ -44,7 +44,7 @@ class GhParams(C.Structure):
     _fields_ = [("m", C.c_double), ("t", C.c_double), ("gs_sweeps", C.c_int32), ("admm_iters", C.c_int32),
                 ("mu", C.c_double), ("form", C.c_int32), ("fp64", C.c_int32), ("diagnostics", C.c_int32),
                 ("early_stop", C.c_int32), ("eps1", C.c_double), ("eps2", C.c_double),
-                ("path_constraints", C.c_int32)]
+                ("path_constraints", C.c_int32), ("cycle_constraints", C.c_int32)]
 
 
 class GeoheatError(RuntimeError):
@@ -126,9 +126,10 @@ def _check(rc: int):
 
 
 def params(m=1.0, t=0.0, gs_sweeps=200, admm_iters=10, mu=100.0, form="edge", fp64=False, diagnostics=False,
-           eps=None, path_constraints=False):
+           eps=None, path_constraints=False, cycle_constraints=False):
     """Solver parameters; eps = (eps1, eps2) turns on early termination of the
-    ADMM; path_constraints adds the multi-source path constraints."""
+    ADMM; path_constraints adds the multi-source path constraints,
+    cycle_constraints the cycle constraints of a closed mesh of genus >= 1."""
     p = GhParams()
     lib().gh_params_default(C.byref(p))
     p.m, p.t, p.gs_sweeps, p.admm_iters, p.mu = m, t, gs_sweeps, admm_iters, mu
@@ -137,6 +138,7 @@ def params(m=1.0, t=0.0, gs_sweeps=200, admm_iters=10, mu=100.0, form="edge", fp
     if eps is not None:
         p.early_stop, p.eps1, p.eps2 = 1, float(eps[0]), float(eps[1])
     p.path_constraints = int(bool(path_constraints))
+    p.cycle_constraints = int(bool(cycle_constraints))
     return p
 
 

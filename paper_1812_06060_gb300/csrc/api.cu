@@ -165,6 +165,10 @@ gh_status validate_params(const gh_params *p) {
         set_error("path_constraints must be 0 or 1");
         return GH_EINVAL;
     }
+    if (p->cycle_constraints != 0 && p->cycle_constraints != 1) {
+        set_error("cycle_constraints must be 0 or 1");
+        return GH_EINVAL;
+    }
     return GH_OK;
 }
 
@@ -381,6 +385,7 @@ void gh_params_default(gh_params *p) {
     p->eps1 = 1e-5;
     p->eps2 = 1e-5;
     p->path_constraints = 0;
+    p->cycle_constraints = 0;
 }
 
 const char *gh_version(void) { return "geoheat 0.1 (sm_103a)"; }
@@ -467,7 +472,7 @@ gh_status gh_mesh_load(gh_ctx ctx, const double *V, int64_t nv, const int32_t *F
         DevMesh &m = mh->h.m;
         DBuf *all[] = {&m.P, &m.F, &m.rowptr, &m.col, &m.col_edge, &m.edges, &m.face_edge, &m.face_sign, &m.edge_face,
                        &m.edge_slot, &m.twin, &m.Af, &m.Av, &m.theta, &m.ev, &m.gradop, &m.Aff, &m.face_rec32,
-                   &m.face_rec64};
+                   &m.face_rec64, &m.cyc_var[0], &m.cyc_var[1], &m.cyc_coef[0], &m.cyc_coef[1]};
         for (DBuf *b : all) dfree(&ctx->c, *b);
         delete mh;
         return s;
@@ -530,7 +535,7 @@ gh_status gh_mesh_free(gh_mesh mesh) {
     DevMesh &m = mesh->h.m;
     DBuf *all[] = {&m.P, &m.F, &m.rowptr, &m.col, &m.col_edge, &m.edges, &m.face_edge, &m.face_sign, &m.edge_face,
                    &m.edge_slot, &m.twin, &m.Af, &m.Av, &m.theta, &m.ev, &m.gradop, &m.Aff, &m.face_rec32,
-                   &m.face_rec64};
+                   &m.face_rec64, &m.cyc_var[0], &m.cyc_var[1], &m.cyc_coef[0], &m.cyc_coef[1]};
     for (DBuf *b : all) dfree(c, *b);
     auto it = std::find(ctx->meshes.begin(), ctx->meshes.end(), mesh);
     if (it != ctx->meshes.end()) ctx->meshes.erase(it);

@@ -154,6 +154,13 @@ struct DevMesh {
     // batch): 0 until tuned on the first solve of that kind, or set by the user
     int bfs_cluster[2] = {0, 0};
     std::shared_ptr<std::mutex> rec_mu = std::make_shared<std::mutex>();   // guards the lazily built parts
+    // cycle constraints of a connected closed surface (Sec. 5.1, cycles.cu),
+    // per form ([0] face, [1] edge): -1 until built on the first solve that
+    // asks for them; constraint j holds entries [cyc_off_h[j], cyc_off_h[j+1])
+    int ncyc[2] = {-1, -1}, cyc_ent[2] = {0, 0};
+    std::vector<int32_t> cyc_off_h[2];
+    DBuf cyc_var[2], cyc_coef[2];
+    std::shared_ptr<std::mutex> cyc_mu = std::make_shared<std::mutex>();
 };
 
 // Per-query workspace (BFS products, the level-ordered layout, solver state).
@@ -241,7 +248,8 @@ gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_d
 // breadth-first sets of every query (each on its own mesh) in one launch
 gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
                   const std::vector<std::vector<int32_t>> &src);
-// the same with a given cluster size (8 is always supported), no tuning
+// the same with a given cluster size (8 is always supported), no tuning; any
+// graph in CSR form works (rowptr, col ascending, col_edge, nv of `meshes`)
 gh_status run_bfs_fixed(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
                         const std::vector<std::vector<int32_t>> &src, int cl);
 bool bfs_cluster_supported(int cl);
@@ -254,9 +262,13 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
 gh_status run_gs(Ctx *c, std::vector<QueryWs *> &ws, cudaEvent_t ev0, cudaEvent_t ev1);
 
 // paths.cu
-// the multi-source path constraints of every item that asks for them; runs
-// before the items' own traversal (it uses their traversal buffers)
+// the multi-source path and cycle constraints of every item that asks for
+// them; runs before the items' own traversal (it uses their traversal buffers)
 gh_status build_path_constraints(Ctx *c, std::vector<Item> &items);
+
+// cycles.cu
+// the cycle constraints of mesh m for one form, built once (DevMesh::ncyc)
+gh_status mesh_cycles(Ctx *c, DevMesh &m, int form);
 
 // stages.cu
 gh_status run_normalize(Ctx *c, const DevMesh &m, QueryWs &q);

@@ -1,5 +1,7 @@
 // Multi-source path constraints (Sec. 5.2, eq. MultiSourceConstraint,
-// eq. MultiSourceConstraintEdgeBased): the per-solve setup.
+// eq. MultiSourceConstraintEdgeBased) and, appended after them, the cycle
+// constraints of a closed mesh (Sec. 5.1, built once per mesh in cycles.cu):
+// the per-solve setup.
 //
 // Paths run from the first (lowest-index) source to each other source.  A
 // path has the fewest edges: the one a breadth-first traversal from the first
@@ -124,9 +126,10 @@ __global__ void __launch_bounds__(PT, 1) k_pc_setup(PcBuild b, double mu, const 
         if (o != i) b.entu[i] = __ldcg(&b.entu[o]);
     }
     __syncthreads();
-    // coefficient rows: one path has at most one entry per edge and at most
-    // two per face (a simple path uses at most two edges of a triangle), so
-    // these sums from zero do not depend on the order of the additions
+    // coefficient rows: a path or cycle has at most one entry per edge and
+    // at most two per face (a simple path uses at most two edges of a
+    // triangle; a loop of faces visits a face once), so these sums from zero
+    // do not depend on the order of the additions
     for (int j = 0; j < npc; ++j)
         for (int i = b.off[j] + tid; i < b.off[j + 1]; i += PT)
             for (int c = 0; c < dim; ++c)
@@ -195,50 +198,68 @@ __global__ void __launch_bounds__(PT, 1) k_pc_setup(PcBuild b, double mu, const 
 
 gh_status build_path_constraints(Ctx *c, std::vector<Item> &items) {
     cudaStream_t st = c->stream;
+    gh_status s;
+    // what every item asks for: its source paths and its mesh's cycles
+    std::vector<int> npath(items.size(), 0), ncyc(items.size(), 0);
     std::vector<DevMesh *> mq;
     std::vector<QueryWs *> wq;
     std::vector<std::vector<int32_t>> sq;
-    std::vector<Item *> it;
-    for (Item &x : items) {
+    std::vector<size_t> need;
+    for (size_t k = 0; k < items.size(); ++k) {
+        Item &x = items[k];
         x.w->pc_n = 0;
         x.w->pc_ent = 0;
-        if (!x.p->path_constraints || x.src->size() < 2) continue;
-        if ((int)x.src->size() > kMaxPc + 1) { set_error("path_constraints takes at most 32 sources"); return GH_EINVAL; }
-        mq.push_back(x.m);
-        wq.push_back(x.w);
-        sq.push_back({(*x.src)[0]});
-        it.push_back(&x);
+        if (x.p->path_constraints && x.src->size() >= 2) npath[k] = (int)x.src->size() - 1;
+        if (x.p->cycle_constraints) {
+            if ((s = mesh_cycles(c, *x.m, x.p->form)) != GH_OK) return s;
+            ncyc[k] = x.m->ncyc[x.p->form == GH_FORM_EDGE ? 1 : 0];
+        }
+        if (npath[k] + ncyc[k] == 0) continue;
+        if (npath[k] + ncyc[k] > kMaxPc) {
+            set_error("at most " + std::to_string(kMaxPc) + " path and cycle constraints per query (" +
+                      std::to_string(npath[k]) + " + " + std::to_string(ncyc[k]) + " asked for)");
+            return GH_EINVAL;
+        }
+        need.push_back(k);
+        if (npath[k]) {
+            mq.push_back(x.m);
+            wq.push_back(x.w);
+            sq.push_back({(*x.src)[0]});
+        }
     }
-    if (it.empty()) return GH_OK;
-    gh_status s;
-    // the traversal from each query's first source (into the query's own
-    // traversal buffers, which its main traversal overwrites afterwards)
-    if ((s = run_bfs_fixed(c, mq, wq, sq, 8)) != GH_OK) return s;
-    const int K = (int)it.size();
-    std::vector<std::vector<int32_t>> lv(K);
-    for (int q = 0; q < K; ++q) {
-        QueryWs &w = *wq[q];
-        const std::vector<int32_t> &src = *it[q]->src;
+    if (need.empty()) return GH_OK;
+    // the traversal from each path query's first source (into the query's
+    // own traversal buffers, which its main traversal overwrites afterwards)
+    if (!mq.empty() && (s = run_bfs_fixed(c, mq, wq, sq, 8)) != GH_OK) return s;
+    std::vector<std::vector<int32_t>> lv(items.size());
+    for (size_t k : need) {
+        if (!npath[k]) continue;
+        QueryWs &w = *items[k].w;
+        const std::vector<int32_t> &src = *items[k].src;
         const int ns = (int)src.size();
         if ((s = dalloc(c, w.pc_src, sizeof(int32_t) * ns)) != GH_OK) return s;
         if ((s = dalloc(c, w.pc_lv, sizeof(int32_t) * ns)) != GH_OK) return s;
         GH_CUDA(cudaMemcpyAsync(w.pc_src.p, src.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st));
         k_pc_levels<<<1, 32, 0, st>>>(ptr<int32_t>(w.pc_src), ns, ptr<int32_t>(w.level), ptr<int32_t>(w.pc_lv));
         ++c->launches;
-        lv[q].resize(ns);
-        GH_CUDA(cudaMemcpyAsync(lv[q].data(), w.pc_lv.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, st));
+        lv[k].resize(ns);
+        GH_CUDA(cudaMemcpyAsync(lv[k].data(), w.pc_lv.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, st));
     }
     GH_CUDA(cudaStreamSynchronize(st));
-    std::vector<std::vector<int32_t>> offs(K);
-    for (int q = 0; q < K; ++q) {
-        QueryWs &w = *wq[q];
-        const DevMesh &m = *mq[q];
-        const int form = it[q]->p->form;
-        const int npc = (int)it[q]->src->size() - 1;
+    std::vector<std::vector<int32_t>> offs(items.size());
+    for (size_t k : need) {
+        QueryWs &w = *items[k].w;
+        DevMesh &m = *items[k].m;
+        const int form = items[k].p->form;
+        const int fi = (form == GH_FORM_EDGE) ? 1 : 0;
+        const int npc = npath[k] + ncyc[k];
         const int dim = (form == GH_FORM_EDGE) ? 1 : 3;
-        std::vector<int32_t> &off = offs[q];
+        // path constraints first (unreachable sources: empty), then the cycles
+        std::vector<int32_t> &off = offs[k];
         off.assign(npc + 1, 0);
-        for (int j = 0; j < npc; ++j) off[j + 1] = off[j] + std::max(lv[q][j + 1], 0);   // unreachable: empty
+        for (int j = 0; j < npath[k]; ++j) off[j + 1] = off[j] + std::max(lv[k][j + 1], 0);
+        const int nent_path = off[npath[k]];
+        for (int j = 0; j < ncyc[k]; ++j) off[npath[k] + j + 1] = nent_path + m.cyc_off_h[fi][j + 1];
         const int nent = off[npc];
         const size_t ne1 = (size_t)std::max(nent, 1);
         const int64_t nvar = (form == GH_FORM_EDGE) ? m.ne : m.nf;
@@ -259,14 +280,23 @@ gh_status build_path_constraints(Ctx *c, std::vector<Item> &items) {
         GH_CUDA(cudaMemcpyAsync(w.pc_off.p, off.data(), sizeof(int32_t) * (npc + 1), cudaMemcpyHostToDevice, st));
         GH_CUDA(cudaMemsetAsync(w.pc_map.p, 0xff, sizeof(int32_t) * nvar, st));
         GH_CUDA(cudaMemsetAsync(w.pc_ucoef.p, 0, sizeof(double) * ne1 * npc * dim, st));
-        k_pc_paths<<<1, 32, 0, st>>>(ptr<int32_t>(w.pc_src), npc, ptr<int32_t>(w.pc_off), ptr<int32_t>(w.parent),
-                                     ptr<int32_t>(w.pedge), ptr<int32_t>(m.edges), ptr<int32_t>(m.edge_face),
-                                     ptr<double>(m.P), form, ptr<int32_t>(w.pc_var), ptr<double>(w.pc_coef));
-        ++c->launches;
+        if (npath[k]) {
+            k_pc_paths<<<1, 32, 0, st>>>(ptr<int32_t>(w.pc_src), npath[k], ptr<int32_t>(w.pc_off),
+                                         ptr<int32_t>(w.parent), ptr<int32_t>(w.pedge), ptr<int32_t>(m.edges),
+                                         ptr<int32_t>(m.edge_face), ptr<double>(m.P), form, ptr<int32_t>(w.pc_var),
+                                         ptr<double>(w.pc_coef));
+            ++c->launches;
+        }
+        if (ncyc[k] && m.cyc_ent[fi] > 0) {
+            GH_CUDA(cudaMemcpyAsync(ptr<int32_t>(w.pc_var) + nent_path, m.cyc_var[fi].p,
+                                    sizeof(int32_t) * m.cyc_ent[fi], cudaMemcpyDeviceToDevice, st));
+            GH_CUDA(cudaMemcpyAsync(ptr<double>(w.pc_coef) + (size_t)nent_path * dim, m.cyc_coef[fi].p,
+                                    sizeof(double) * m.cyc_ent[fi] * dim, cudaMemcpyDeviceToDevice, st));
+        }
         PcBuild b{npc, dim, nent, form, ptr<int32_t>(w.pc_off), ptr<int32_t>(w.pc_var), ptr<double>(w.pc_coef),
                   ptr<int32_t>(w.pc_entu), ptr<int32_t>(w.pc_uvar), ptr<int32_t>(w.pc_meta), ptr<int32_t>(w.pc_drop),
                   ptr<int32_t>(w.pc_map), ptr<double>(w.pc_ucoef), ptr<double>(w.pc_dinv), ptr<double>(w.pc_L)};
-        k_pc_setup<<<1, PT, 0, st>>>(b, it[q]->p->mu, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.twin),
+        k_pc_setup<<<1, PT, 0, st>>>(b, items[k].p->mu, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.twin),
                                      ptr<double>(m.Af));
         ++c->launches;
         w.pc_n = npc;
