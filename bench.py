@@ -162,15 +162,20 @@ def stage_bytes(nv: int, ne: int, nf: int, sweeps: int, iters: int, form: str, n
         48 per face for the first iteration, which starts from g = h, lambda = 0
         and reads h in their place
       edge ADMM: 78 per face + 32 per edge to initialise, per iteration 69 per
-        face (face pass: x, lambda, w, signs) + 44 per edge (edge pass)
-      integration: 64 (edge form) or 112 (face form) per vertex for the
-        increments, 36 per vertex for each of ceil(log2 L) jumping rounds"""
+        face (face pass: x, lambda, w, signs) + 40 per edge (edge pass: the
+        edge's faces and slots, sum of targets, w, lambda, x written)
+      integration: the increments, 40 (edge form: set index, pairing vertex
+        and edge, one end of that edge, its x, increment, link and distance
+        written) or 88 (face form: the same with the edge's two faces, the
+        positions and g in place of x) per vertex, then 24 per vertex for
+        each of ceil(log2 L) pointer-jumping rounds (distance and link read
+        and written; the gathered elements of the same arrays count once)"""
     import math
     rows = 2 * ne
-    adm = (max(iters, 1) * 154 * nf - 48 * nf) if form == "face" else (78 * nf + 32 * ne + iters * (69 * nf + 44 * ne))
+    adm = (max(iters, 1) * 154 * nf - 48 * nf) if form == "face" else (78 * nf + 32 * ne + iters * (69 * nf + 40 * ne))
     rounds = max(1, math.ceil(math.log2(max(nlev, 2))))
     return {"bfs_layout": 88 * nv + 52 * rows, "diffusion": gs_bytes(nv, ne, sweeps), "normalize": 66 * nf,
-            "admm": adm, "integrate": (64 if form == "edge" else 112) * nv + 36 * nv * rounds}
+            "admm": adm, "integrate": (40 if form == "edge" else 88) * nv + 24 * nv * rounds}
 
 
 def stage_roofline(stage_ms, nbytes, peak):
