@@ -13,6 +13,8 @@
 // of a batch).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gh {
@@ -84,12 +86,11 @@ __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
 //           CTA barrier it records their row bounds and offers their keys to
 //           their neighbours (64-bit atomicMin) without waiting for the other
 //           CTAs; cluster barrier.
-// When the ownership grows lopsided (a set of at least kRebalance vertices
-// with one CTA owning more than twice its share: a single source starts in
-// one CTA), the set is split evenly instead, after one more cluster barrier.
-// Every prefix involved runs in rank order, so the queue is exactly the
-// FIFO order.
-constexpr int kRebalance = 256;
+// When the ownership grows lopsided (the busiest CTA would own more than 64
+// parents above an even share, or need more chunks of BT parents: a single
+// source starts in one CTA, and a set's time follows its busiest CTA), the
+// set is split evenly instead, after one more cluster barrier.  Every prefix
+// involved runs in rank order, so the queue is exactly the FIFO order.
 
 __device__ __forceinline__ unsigned long long bfs_key(int r, int slot) {
     return ((unsigned long long)(unsigned)(r + 1) << 32) | (unsigned)slot;
@@ -318,10 +319,10 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
             base_run += tot;
         }
         // the next set's parents of this CTA: its own children, or an even
-        // split when one CTA would own more than twice its share
-        if (total >= kRebalance && most * CL > 2 * total) {
+        // split when the ownership is lopsided
+        const int per = (total + CL - 1) / CL;
+        if (most - per > 64 || (most + BT - 1) / BT > (per + BT - 1) / BT) {
             cluster.sync();   // every CTA's children are written
-            const int per = (total + CL - 1) / CL;
             plo = min(hi + total, hi + crank * per);
             phi = min(hi + total, plo + per);
         } else {
@@ -589,8 +590,8 @@ gh_status run_bfs_fixed(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs 
 
 // The breadth-first sets of every query.  The cluster size is tuned per mesh,
 // separately for single queries and batches: the first solve of each kind
-// runs every size the device supports twice (alternating), timed with
-// events, and keeps the fastest (all sizes give the same sets and order, so the last run's
+// runs every size the device supports, timed with events (a second,
+// alternating round when the first is close), and keeps the fastest (all sizes give the same sets and order, so the last run's
 // result is the solve's).  A batch over several meshes uses clusters of 8.
 gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
                   const std::vector<std::vector<int32_t>> &src) {
@@ -609,11 +610,17 @@ gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws
     cudaEvent_t e0, e1;
     GH_CUDA(cudaEventCreate(&e0));
     GH_CUDA(cudaEventCreate(&e1));
-    // two alternating rounds, each candidate's faster run counts: the first
-    // launch of a solve runs on cold caches and would bias a single round
+    // up to two alternating rounds, each candidate's faster run counting: the
+    // first launch of a solve runs on cold caches and can bias one round; the
+    // second round runs only when the first is within 15 %
     std::vector<float> best_ms(cand.size(), 0.0f);
     gh_status s = GH_OK;
     for (int round = 0; round < 2 && s == GH_OK; ++round) {
+        if (round == 1) {
+            const float lo = *std::min_element(best_ms.begin(), best_ms.end());
+            const float hi = *std::max_element(best_ms.begin(), best_ms.end());
+            if (hi > 1.15f * lo) break;
+        }
         for (size_t i = 0; i < cand.size(); ++i) {
             cudaEventRecord(e0, c->stream);
             if ((s = run_bfs_once(c, mq, ws, src, cand[i])) != GH_OK) break;   // synchronises the stream
