@@ -9,7 +9,8 @@ it with gcc, loads it with ctypes and chains the steps of Algorithm 1.
 Parity status of each function (pins in tests/test_oracle_*.py):
   connectivity, geometry, bfs, gs, normalize, face_admm, edge_admm,
   integrate_face, integrate_edge, source_paths, path_constraints and the
-  path-constrained ADMM: pinned.
+  path-constrained ADMM, cycle_constraints; idt.py (the intrinsic Delaunay
+  triangulation and the edge form on it): pinned.
 """
 from __future__ import annotations
 
@@ -80,7 +81,7 @@ def _declare(L):
     L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P, P, P]
     L.orc_edge_admm.restype = C.c_int
     L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P,
-                                P, P, P]
+                                P, P, P, P]
     L.orc_integrate_face.restype = C.c_int
     L.orc_integrate_face.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
     L.orc_integrate_edge.restype = C.c_int
@@ -120,6 +121,8 @@ class MeshData:
     cot: np.ndarray
     theta: np.ndarray
     hbar: float
+    elen: np.ndarray | None = None     # intrinsic meshes: edge lengths
+    frame: np.ndarray | None = None    # intrinsic meshes: [nf,3,2] corner coordinates in each face's frame
 
     @property
     def nv(self):
@@ -249,15 +252,17 @@ def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
     return g, y, lam, res[:done.value]
 
 
-def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
+def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None, z_in=None):
     """Edge-based ADMM (Sec. 4.1).  Returns x [ne], w [nf,3], lambda [nf,3],
     z [nf,3] and residuals [iterations run, 2].  eps = (eps1, eps2) stops
     once both residuals are within |Z|_F * eps (the targets' norm standing
     in for Sec. 3.2's |M|_F); None runs all iters.  pc =
     path_constraints(md, sources, "edge") adds the multi-source constraints
-    of Sec. 5.2."""
+    of Sec. 5.2.  z_in [nf,3] gives the target differences instead of h . e
+    (an intrinsic triangulation, Sec. 5.3)."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     npc, off, var, coef = _pc_args(pc, 1)
+    zi = None if z_in is None else np.ascontiguousarray(z_in, dtype=np.float64)
     x = np.empty(md.ne)
     w = np.empty((md.nf, 3))
     lam = np.empty((md.nf, 3))
@@ -267,8 +272,9 @@ def edge_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
     e1, e2 = eps if eps is not None else (0.0, 0.0)
     _check(lib().orc_edge_admm(md.nv, _p(md.P), md.nf, _p(md.F), md.ne, _p(md.edges), _p(md.flip),
                                _p(md.face_edge), _p(md.face_sign), _p(md.edge_face), _p(md.edge_slot), _p(h),
-                               iters, mu, e1, e2, int(eps is not None), npc, _p(off), _p(var), _p(coef), _p(x),
-                               _p(w), _p(lam), _p(z), _p(res), C.byref(done)), "orc_edge_admm")
+                               iters, mu, e1, e2, int(eps is not None), npc, _p(off), _p(var), _p(coef),
+                               None if zi is None else _p(zi), _p(x), _p(w), _p(lam), _p(z), _p(res),
+                               C.byref(done)), "orc_edge_admm")
     return x, w, lam, z, res[:done.value]
 
 

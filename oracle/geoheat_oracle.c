@@ -680,7 +680,9 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
 
 /*
  * Target differences z = Z[3f+k] = h_f . e, e the vector of the orientation
- * halfedge (head - tail) of local edge k (eq. TargetDifference).
+ * halfedge (head - tail) of local edge k (eq. TargetDifference); z_in
+ * (nullable) gives them instead (an intrinsic triangulation, whose edge
+ * vectors live in each face's own frame, Sec. 5.3).
  * Minimises 1/2 sum_e sum_{h in H_e} (x_e - h_e)^2 subject to
  * sum_k s_k^f x_{e_k^f} = 0 on every face (eq. Integrability), split as
  * W - R X = 0.  Initialisation: lambda = 0, x_e = mean of its targets,
@@ -696,7 +698,8 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
                   const uint8_t *flip, const int32_t *face_edge, const int8_t *face_sign, const int32_t *edge_face,
                   const int32_t *edge_slot, const double *h, int32_t iters, double mu, double eps1, double eps2,
                   int32_t early_stop, int32_t npc, const int32_t *pc_off, const int32_t *pc_var,
-                  const double *pc_coef, double *x, double *w, double *lam, double *z, double *res, int32_t *done) {
+                  const double *pc_coef, const double *z_in, double *x, double *w, double *lam, double *z,
+                  double *res, int32_t *done) {
     (void)nv; (void)F;
     if (npc < 0 || npc > 64) return ORC_EINVAL;
     orc_pc pc;
@@ -712,6 +715,10 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
     if (!xold) { pc_free(&pc); return ORC_ENOMEM; }
     for (int64_t f = 0; f < nf; ++f) {
         for (int k = 0; k < 3; ++k) {
+            if (z_in) {   /* targets given (an intrinsic triangulation's local frames) */
+                z[3 * f + k] = z_in[3 * f + k];
+                continue;
+            }
             int64_t e = face_edge[3 * f + k];
             int32_t ta, hd;
             eta(edges, flip, e, &ta, &hd);
