@@ -184,6 +184,24 @@ gh_status gh_mesh_info(gh_mesh mesh, int64_t *nv, int64_t *ne, int64_t *nf, doub
 gh_status gh_mesh_tuning(gh_mesh mesh, int32_t *bfs_cluster);
 gh_status gh_mesh_set_tuning(gh_mesh mesh, int32_t kind, int32_t bfs_cluster);
 
+/*
+ * Replaces the mesh's triangulation by its intrinsic Delaunay triangulation
+ * (Sec. 5.3): edge flips by the opposite-angle criterion (an interior edge
+ * whose opposite angles sum to more than pi, beyond a 1e-12 tolerance on
+ * their cotangents, is flipped; the new edge's length comes from the two
+ * triangles unfolded into the plane) until none is left.  A flip that would
+ * join two vertices already joined is left out.  Afterwards the mesh is the
+ * face list plus edge lengths: the diffusion uses cotangents and vertex areas
+ * from the lengths, normalisation and the edge form's target differences use
+ * each face's own frame, and only the edge form solves on it (GH_EINVAL for
+ * the face form).  The vertices and their indices are unchanged; faces and
+ * edges are those of the new triangulation (GH_DUMP_FACES, GH_DUMP_EDGES,
+ * GH_DUMP_ELEN).  flips (nullable) receives the number of flips.
+ * GH_EINVAL if the mesh is already intrinsic, GH_EBUSY while serving
+ * requests on it are in flight.
+ */
+gh_status gh_mesh_intrinsic_delaunay(gh_mesh mesh, int64_t *flips);
+
 /* Frees the mesh; GH_EBUSY while serving requests on it are in flight. */
 gh_status gh_mesh_free(gh_mesh mesh);
 
@@ -266,7 +284,9 @@ typedef enum {
     GH_DUMP_ITERS = 21,     /* int32 [1]     ADMM iterations run (early_stop can end them before admm_iters) */
     GH_DUMP_PC_OFF = 22,    /* int32 [npc+1] path constraints: entries of constraint j are [off[j], off[j+1]) */
     GH_DUMP_PC_VAR = 23,    /* int32 [n]     constrained variable of each entry: edge id (edge form), face id (face form) */
-    GH_DUMP_PC_COEF = 24    /* float64 [n][dim] coefficient of each entry: sign (edge form), path edge vector (face form) */
+    GH_DUMP_PC_COEF = 24,   /* float64 [n][dim] coefficient of each entry: sign (edge form), path edge vector (face form) */
+    GH_DUMP_FACES = 25,     /* int32 [nf][3] the faces of the mesh's triangulation */
+    GH_DUMP_ELEN = 26       /* float64 [ne]  edge lengths */
 } gh_dump_item;
 
 gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *count, int32_t *elem_bytes);

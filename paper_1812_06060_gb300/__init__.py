@@ -27,7 +27,7 @@ GH_FORM_FACE, GH_FORM_EDGE = 0, 1
 (GH_DUMP_LEVEL, GH_DUMP_PARENT, GH_DUMP_ORDER, GH_DUMP_LEVEL_OFF, GH_DUMP_U_MANT, GH_DUMP_U_EXP, GH_DUMP_H,
  GH_DUMP_G, GH_DUMP_X, GH_DUMP_D, GH_DUMP_EDGES, GH_DUMP_FACE_EDGE, GH_DUMP_FACE_SIGN, GH_DUMP_THETA, GH_DUMP_AV,
  GH_DUMP_AF, GH_DUMP_ROWPTR, GH_DUMP_COL, GH_DUMP_RESID, GH_DUMP_E1, GH_DUMP_T, GH_DUMP_ITERS, GH_DUMP_PC_OFF,
- GH_DUMP_PC_VAR, GH_DUMP_PC_COEF) = range(25)
+ GH_DUMP_PC_VAR, GH_DUMP_PC_COEF, GH_DUMP_FACES, GH_DUMP_ELEN) = range(27)
 
 STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: "GH_ETIMEOUT", 5: "GH_EBUSY",
                 6: "GH_ENOTFOUND", 7: "GH_ENONMANIFOLD"}
@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: 
 # symbols declared in include/geoheat.h
 EXPORTS = ["gh_params_default", "gh_version", "gh_ctx_create", "gh_ctx_destroy", "gh_ctx_set_stream", "gh_ctx_set_wait_limit", "gh_ctx_memory",
            "gh_ctx_stats",
-           "gh_mesh_load", "gh_mesh_info", "gh_mesh_tuning", "gh_mesh_set_tuning", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
+           "gh_mesh_load", "gh_mesh_info", "gh_mesh_tuning", "gh_mesh_set_tuning", "gh_mesh_intrinsic_delaunay", "gh_mesh_free", "gh_solve", "gh_solve_batch", "gh_debug_size",
            "gh_debug_dump", "gh_stage_times", "gh_mean_edge_length_noalloc", "gh_serve_config", "gh_submit", "gh_poll",
            "gh_wait", "gh_last_error"]
 
@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     L.gh_mesh_tuning.argtypes = [P, C.POINTER(I32)]
     L.gh_mesh_set_tuning.restype = S
     L.gh_mesh_set_tuning.argtypes = [P, I32, I32]
+    L.gh_mesh_intrinsic_delaunay.restype = S
+    L.gh_mesh_intrinsic_delaunay.argtypes = [P, C.POINTER(I64)]
     L.gh_mesh_free.restype = S
     L.gh_mesh_free.argtypes = [P]
     L.gh_solve.restype = S
@@ -248,6 +250,13 @@ class Mesh:
         src = np.ascontiguousarray(np.concatenate([np.asarray(s, np.int32) for s in source_sets]), dtype=np.int32)
         _check(lib().gh_solve_batch(self.handle, _addr(off), _addr(src), len(source_sets), C.byref(prm), _addr(out)))
         return out
+
+    def intrinsic_delaunay(self) -> int:
+        """Replace the triangulation by its intrinsic Delaunay triangulation
+        (gh_mesh_intrinsic_delaunay); returns the number of flips."""
+        n = C.c_int64()
+        _check(lib().gh_mesh_intrinsic_delaunay(self.handle, C.byref(n)))
+        return n.value
 
     def tuning(self) -> tuple:
         """Breadth-first cluster sizes in use (single query, batch); 0 = not tuned yet."""

@@ -192,6 +192,10 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
     const int K = (int)items.size();
     gh_status s = GH_OK;
     for (Item &it : items) {
+        if (it.m->intrinsic && it.p->form == GH_FORM_FACE) {
+            set_error("an intrinsic triangulation solves in the edge form only (Sec. 5.3)");
+            return GH_EINVAL;
+        }
         if ((s = ensure_ws(c, *it.m, *it.w, it.p->fp64, it.p->form, it.p->admm_iters)) != GH_OK) return s;
         it.w->diagnostics = it.p->diagnostics;
         it.w->sweeps = it.p->gs_sweeps;
@@ -472,7 +476,8 @@ gh_status gh_mesh_load(gh_ctx ctx, const double *V, int64_t nv, const int32_t *F
         DevMesh &m = mh->h.m;
         DBuf *all[] = {&m.P, &m.F, &m.rowptr, &m.col, &m.col_edge, &m.edges, &m.face_edge, &m.face_sign, &m.edge_face,
                        &m.edge_slot, &m.twin, &m.Af, &m.Av, &m.theta, &m.ev, &m.gradop, &m.Aff, &m.face_rec32,
-                   &m.face_rec64, &m.cyc_var[0], &m.cyc_var[1], &m.cyc_coef[0], &m.cyc_coef[1]};
+                   &m.face_rec64, &m.cyc_var[0], &m.cyc_var[1], &m.cyc_coef[0], &m.cyc_coef[1], &m.elen, &m.gradop64,
+                   &m.evf64, &m.evf32};
         for (DBuf *b : all) dfree(&ctx->c, *b);
         delete mh;
         return s;
@@ -498,6 +503,14 @@ gh_status gh_mesh_tuning(gh_mesh mesh, int32_t *bfs_cluster) {
     bfs_cluster[0] = m.bfs_cluster[0];
     bfs_cluster[1] = m.bfs_cluster[1];
     return GH_OK;
+}
+
+gh_status gh_mesh_intrinsic_delaunay(gh_mesh mesh, int64_t *flips) {
+    if (!mesh) { set_error("mesh is NULL"); return GH_EINVAL; }
+    std::lock_guard<std::mutex> lk(mesh->ctx->mu);
+    if (mesh->h.inflight.load() > 0) { set_error("mesh has serving requests in flight"); return GH_EBUSY; }
+    GH_CUDA(cudaSetDevice(mesh->ctx->c.device));
+    return mesh_intrinsic_delaunay(&mesh->ctx->c, mesh->h.m, flips);
 }
 
 gh_status gh_mesh_set_tuning(gh_mesh mesh, int32_t kind, int32_t bfs_cluster) {
@@ -535,7 +548,8 @@ gh_status gh_mesh_free(gh_mesh mesh) {
     DevMesh &m = mesh->h.m;
     DBuf *all[] = {&m.P, &m.F, &m.rowptr, &m.col, &m.col_edge, &m.edges, &m.face_edge, &m.face_sign, &m.edge_face,
                    &m.edge_slot, &m.twin, &m.Af, &m.Av, &m.theta, &m.ev, &m.gradop, &m.Aff, &m.face_rec32,
-                   &m.face_rec64, &m.cyc_var[0], &m.cyc_var[1], &m.cyc_coef[0], &m.cyc_coef[1]};
+                   &m.face_rec64, &m.cyc_var[0], &m.cyc_var[1], &m.cyc_coef[0], &m.cyc_coef[1], &m.elen, &m.gradop64,
+                   &m.evf64, &m.evf32};
     for (DBuf *b : all) dfree(c, *b);
     auto it = std::find(ctx->meshes.begin(), ctx->meshes.end(), mesh);
     if (it != ctx->meshes.end()) ctx->meshes.erase(it);
@@ -578,7 +592,7 @@ gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *coun
     QueryWs *w = (query >= 0 && query < (int)mesh->h.ws.size()) ? mesh->h.ws[query] : nullptr;
     bool need_q = !(what == GH_DUMP_EDGES || what == GH_DUMP_FACE_EDGE || what == GH_DUMP_FACE_SIGN ||
                     what == GH_DUMP_THETA || what == GH_DUMP_AV || what == GH_DUMP_AF || what == GH_DUMP_ROWPTR ||
-                    what == GH_DUMP_COL);
+                    what == GH_DUMP_COL || what == GH_DUMP_FACES || what == GH_DUMP_ELEN);
     if (need_q && (!w || !w->level.p)) { set_error("no such query in the last solve"); return GH_EINVAL; }
     int64_t n = 0;
     int32_t eb = 4;
@@ -610,6 +624,8 @@ gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *coun
     case GH_DUMP_PC_OFF: n = w->pc_n ? w->pc_n + 1 : 0; break;
     case GH_DUMP_PC_VAR: n = w->pc_ent; break;
     case GH_DUMP_PC_COEF: n = (int64_t)w->pc_ent * w->pc_dim; eb = 8; break;
+    case GH_DUMP_FACES: n = 3 * m.nf; break;
+    case GH_DUMP_ELEN: n = m.ne; eb = 8; break;
     default: set_error("unknown dump item"); return GH_EINVAL;
     }
     *count = n;
@@ -695,6 +711,8 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out) {
     case GH_DUMP_PC_OFF: return n ? cp(w->pc_off, 4 * n) : GH_OK;
     case GH_DUMP_PC_VAR: return n ? cp(w->pc_var, 4 * n) : GH_OK;
     case GH_DUMP_PC_COEF: return n ? cp(w->pc_coef, 8 * n) : GH_OK;
+    case GH_DUMP_FACES: return cp(m.F, 4 * n);
+    case GH_DUMP_ELEN: return cp(m.elen, 8 * n);
     default: set_error("unknown dump item"); return GH_EINVAL;
     }
 }

@@ -150,6 +150,14 @@ struct DevMesh {
     // twin weight A'/(A + A'), then sqrt(A_f): 16 values (FP32 and FP64
     // copies), built on the first face-form solve
     DBuf face_rec32, face_rec64;
+    DBuf elen;       // double [ne] edge lengths
+    // an intrinsic triangulation (Sec. 5.3, gh_mesh_intrinsic_delaunay): the
+    // triangulation is the face list plus the lengths; per face, in its own
+    // frame, the hat-function gradients and the edge vectors of the three
+    // slots (lower -> higher vertex), FP64 and FP32 (gradop holds the FP32
+    // gradients); P keeps the input positions, which no longer define edges
+    int intrinsic = 0;
+    DBuf gradop64, evf64, evf32;
     // breadth-first cluster size per kind of solve ([0] one query, [1] a
     // batch): 0 until tuned on the first solve of that kind, or set by the user
     int bfs_cluster[2] = {0, 0};
@@ -243,6 +251,16 @@ gh_status exclusive_scan_u32_dev(Ctx *c, const int32_t *in, int32_t *out, int64_
 
 // setup.cu
 gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_dev);
+// the stages of build_mesh: connectivity of m.F; geometry from m.P; and the
+// geometry of an intrinsic triangulation from the lengths L[3f+k] of the edge
+// opposite corner k of every face (device, FP64)
+gh_status build_connectivity(Ctx *c, DevMesh &m);
+gh_status build_geometry_positions(Ctx *c, DevMesh &m);
+gh_status build_geometry_lengths(Ctx *c, DevMesh &m, const double *L);
+
+// idt.cu
+// replaces m's triangulation by its intrinsic Delaunay triangulation
+gh_status mesh_intrinsic_delaunay(Ctx *c, DevMesh &m, int64_t *flips);
 
 // bfs.cu
 // breadth-first sets of every query (each on its own mesh) in one launch
@@ -282,5 +300,16 @@ int *dev_status(Ctx *c);
 gh_status check_status(Ctx *c, const char *stage);
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// triangle area from its side lengths in Kahan's arrangement of Heron's
+// formula (sides sorted a >= b >= c)
+__device__ inline double heron_d(double a, double b, double c) {
+    double t;
+    if (a < b) { t = a; a = b; b = t; }
+    if (b < c) { t = b; b = c; c = t; }
+    if (a < b) { t = a; a = b; b = t; }
+    const double q = (a + (b + c)) * (c - (a - b)) * (c + (a - b)) * (a + (b - c));
+    return 0.25 * sqrt(q > 0.0 ? q : 0.0);
+}
 
 }  // namespace gh

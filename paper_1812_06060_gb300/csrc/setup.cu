@@ -209,6 +209,63 @@ __global__ void k_edge_geom(const double *__restrict__ P, const int32_t *__restr
     elen[e] = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 }
 
+// per face of an intrinsic triangulation, from the lengths L[3f+k] of the
+// edge opposite corner k: area, corner cotangents (l1^2 + l2^2 - l_opp^2)/(4A),
+// and in the face's own frame (corner 0 at the origin, corner 1 on the +x
+// axis, corner 2 above) the hat-function gradients (N x e_k)/(2A), N = +z,
+// and the slot edge vectors oriented from the lower to the higher vertex
+__global__ void k_face_geom_len(const int32_t *__restrict__ F, const double *__restrict__ L, int64_t nf, double *Af,
+                                float *Aff, double *cot, float *gradop, double *gradop64, double *evf64,
+                                float *evf32) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const double l[3] = {L[3 * f], L[3 * f + 1], L[3 * f + 2]};
+    const double A = heron_d(l[0], l[1], l[2]);
+    Af[f] = A;
+    Aff[f] = (float)A;
+    const double x2 = (l[2] * l[2] + l[1] * l[1] - l[0] * l[0]) / (2.0 * l[2]);
+    const double y2s = l[1] * l[1] - x2 * x2;
+    const double q[3][2] = {{0.0, 0.0}, {l[2], 0.0}, {x2, sqrt(y2s > 0.0 ? y2s : 0.0)}};
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        cot[3 * f + k] = (l[i] * l[i] + l[j] * l[j] - l[k] * l[k]) / (4.0 * A);
+        const double e[2] = {q[j][0] - q[i][0], q[j][1] - q[i][1]};
+        const double g[2] = {-e[1] / (2.0 * A), e[0] / (2.0 * A)};
+        gradop64[9 * f + 3 * k] = g[0];
+        gradop64[9 * f + 3 * k + 1] = g[1];
+        gradop64[9 * f + 3 * k + 2] = 0.0;
+        gradop[9 * f + 3 * k] = (float)g[0];
+        gradop[9 * f + 3 * k + 1] = (float)g[1];
+        gradop[9 * f + 3 * k + 2] = 0.0f;
+        const bool fwd = F[3 * f + i] < F[3 * f + j];
+        const int t = fwd ? i : j, h = fwd ? j : i;
+        const double v[2] = {q[h][0] - q[t][0], q[h][1] - q[t][1]};
+        evf64[9 * f + 3 * k] = v[0];
+        evf64[9 * f + 3 * k + 1] = v[1];
+        evf64[9 * f + 3 * k + 2] = 0.0;
+        evf32[9 * f + 3 * k] = (float)v[0];
+        evf32[9 * f + 3 * k + 1] = (float)v[1];
+        evf32[9 * f + 3 * k + 2] = 0.0f;
+    }
+}
+
+// per edge of an intrinsic triangulation: theta_e = 1/2 sum cot(opposite
+// corner), the length (from its first face) and no ambient edge vector
+__global__ void k_edge_geom_len(int64_t ne, const int32_t *__restrict__ edge_face, const int32_t *__restrict__ edge_slot,
+                                const double *__restrict__ cot, const double *__restrict__ L, double *theta, float *ev,
+                                double *elen) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    double th = 0.0;
+    for (int j = 0; j < 2; ++j) {
+        int f = edge_face[2 * e + j];
+        if (f >= 0) th += 0.5 * cot[3 * f + edge_slot[2 * e + j]];
+    }
+    theta[e] = th;
+    elen[e] = L[3 * edge_face[2 * e] + edge_slot[2 * e]];
+    ev[3 * e] = ev[3 * e + 1] = ev[3 * e + 2] = 0.0f;
+}
+
 // A_v = 1/3 of the incident face area.  Every face at v has exactly two edges
 // at v, so A_v = 1/6 sum over v's edges of the areas of their faces: a
 // deterministic gather.
@@ -246,6 +303,24 @@ __global__ void k_sum_partial(const double *__restrict__ x, int64_t n, int64_t p
 
 }  // namespace
 
+// mean of x[0..n) with a fixed summation order
+static gh_status det_mean(Ctx *c, const double *x, int64_t n, double *out) {
+    cudaStream_t st = c->stream;
+    const int64_t per_block = 65536;
+    int64_t nb = (n + per_block - 1) / per_block;
+    DBuf part;
+    gh_status s;
+    if ((s = dalloc(c, part, sizeof(double) * (nb + 1))) != GH_OK) return s;
+    k_sum_partial<<<(unsigned)nb, RB, 0, st>>>(x, n, per_block, ptr<double>(part)); ++c->launches;
+    k_sum_partial<<<1, RB, 0, st>>>(ptr<double>(part), nb, nb, ptr<double>(part) + nb); ++c->launches;
+    double total = 0.0;
+    GH_CUDA(cudaMemcpyAsync(&total, ptr<double>(part) + nb, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GH_CUDA(cudaStreamSynchronize(st));
+    dfree(c, part);
+    *out = total / (double)n;
+    return GH_OK;
+}
+
 gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_dev) {
     cudaStream_t st = c->stream;
     const int T = 256;
@@ -257,9 +332,20 @@ gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_d
     if ((s = dalloc(c, m.F, sizeof(int32_t) * 3 * nf)) != GH_OK) return s;
     GH_CUDA(cudaMemcpyAsync(m.P.p, V_dev, sizeof(double) * 3 * nv, cudaMemcpyDefault, st));
     GH_CUDA(cudaMemcpyAsync(m.F.p, F_dev, sizeof(int32_t) * 3 * nf, cudaMemcpyDefault, st));
-    const int32_t *F = ptr<int32_t>(m.F);
-    k_check_faces<<<blocks_for(nf, T), T, 0, st>>>(F, nf, nv, err); ++c->launches;
+    k_check_faces<<<blocks_for(nf, T), T, 0, st>>>(ptr<int32_t>(m.F), nf, nv, err); ++c->launches;
     if ((s = check_status(c, "face indices")) != GH_OK) return s;
+    if ((s = build_connectivity(c, m)) != GH_OK) return s;
+    return build_geometry_positions(c, m);
+}
+
+gh_status build_connectivity(Ctx *c, DevMesh &m) {
+    cudaStream_t st = c->stream;
+    const int T = 256;
+    int64_t nv = m.nv, nf = m.nf;
+    int *err = dev_status(c);
+    GH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    gh_status s;
+    const int32_t *F = ptr<int32_t>(m.F);
 
     // duplicated rows -> sorted distinct rows
     DBuf cnt, dptr, fill, dcol, deg, up, eoff;
@@ -314,11 +400,18 @@ gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_d
                                                  ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
                                                  ptr<int32_t>(m.twin), err); ++c->launches;
     cleanup2();
-    if ((s = check_status(c, "edge-face incidence")) != GH_OK) return s;
+    return check_status(c, "edge-face incidence");
+}
 
+gh_status build_geometry_positions(Ctx *c, DevMesh &m) {
+    cudaStream_t st = c->stream;
+    const int T = 256;
+    const int64_t nv = m.nv, nf = m.nf, ne = m.ne;
+    const int32_t *F = ptr<int32_t>(m.F);
+    gh_status s;
     // geometry, FP64
-    DBuf cot, elen, part;
-    auto cleanup3 = [&]() { dfree(c, cot); dfree(c, elen); dfree(c, part); };
+    DBuf cot;
+    auto cleanup3 = [&]() { dfree(c, cot); };
     if ((s = dalloc(c, m.Af, sizeof(double) * nf)) != GH_OK) return s;
     if ((s = dalloc(c, m.Aff, sizeof(float) * nf)) != GH_OK) return s;
     if ((s = dalloc(c, m.Av, sizeof(double) * nv)) != GH_OK) return s;
@@ -326,26 +419,52 @@ gh_status build_mesh(Ctx *c, DevMesh &m, const double *V_dev, const int32_t *F_d
     if ((s = dalloc(c, m.ev, sizeof(float) * 3 * ne)) != GH_OK) return s;
     if ((s = dalloc(c, m.gradop, sizeof(float) * 9 * nf)) != GH_OK) return s;
     if ((s = dalloc(c, cot, sizeof(double) * 3 * nf)) != GH_OK) { cleanup3(); return s; }
-    if ((s = dalloc(c, elen, sizeof(double) * ne)) != GH_OK) { cleanup3(); return s; }
+    if ((s = dalloc(c, m.elen, sizeof(double) * ne)) != GH_OK) { cleanup3(); return s; }
     k_face_geom<<<blocks_for(nf, T), T, 0, st>>>(ptr<double>(m.P), F, nf, ptr<double>(m.Af), ptr<float>(m.Aff),
                                                 ptr<double>(cot), ptr<float>(m.gradop)); ++c->launches;
     k_edge_geom<<<blocks_for(ne, T), T, 0, st>>>(ptr<double>(m.P), ptr<int32_t>(m.edges), ne, ptr<int32_t>(m.edge_face),
                                                 ptr<int32_t>(m.edge_slot), ptr<double>(cot), ptr<double>(m.theta),
-                                                ptr<float>(m.ev), ptr<double>(elen)); ++c->launches;
+                                                ptr<float>(m.ev), ptr<double>(m.elen)); ++c->launches;
     k_vertex_area<<<blocks_for(nv, T), T, 0, st>>>(ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col_edge), nv,
                                                   ptr<int32_t>(m.edge_face), ptr<double>(m.Af), ptr<double>(m.Av)); ++c->launches;
     // mean edge length: fixed chunks, fixed tree order, then one block
-    const int64_t per_block = 65536;
-    int64_t nb = (ne + per_block - 1) / per_block;
-    if ((s = dalloc(c, part, sizeof(double) * (nb + 1))) != GH_OK) { cleanup3(); return s; }
-    k_sum_partial<<<(unsigned)nb, RB, 0, st>>>(ptr<double>(elen), ne, per_block, ptr<double>(part)); ++c->launches;
-    k_sum_partial<<<1, RB, 0, st>>>(ptr<double>(part), nb, nb, ptr<double>(part) + nb); ++c->launches;
-    double total = 0.0;
-    GH_CUDA(cudaMemcpyAsync(&total, ptr<double>(part) + nb, sizeof(double), cudaMemcpyDeviceToHost, st));
-    GH_CUDA(cudaStreamSynchronize(st));
     cleanup3();
-    m.hbar = total / (double)ne;
+    if ((s = det_mean(c, ptr<double>(m.elen), ne, &m.hbar)) != GH_OK) return s;
     return check_status(c, "geometry");
+}
+
+}  // namespace gh
+
+namespace gh {
+
+gh_status build_geometry_lengths(Ctx *c, DevMesh &m, const double *L) {
+    cudaStream_t st = c->stream;
+    const int T = 256;
+    const int64_t nv = m.nv, nf = m.nf, ne = m.ne;
+    gh_status s;
+    DBuf cot;
+    if ((s = dalloc(c, m.Af, sizeof(double) * nf)) != GH_OK) return s;
+    if ((s = dalloc(c, m.Aff, sizeof(float) * nf)) != GH_OK) return s;
+    if ((s = dalloc(c, m.Av, sizeof(double) * nv)) != GH_OK) return s;
+    if ((s = dalloc(c, m.theta, sizeof(double) * ne)) != GH_OK) return s;
+    if ((s = dalloc(c, m.ev, sizeof(float) * 3 * ne)) != GH_OK) return s;
+    if ((s = dalloc(c, m.gradop, sizeof(float) * 9 * nf)) != GH_OK) return s;
+    if ((s = dalloc(c, m.gradop64, sizeof(double) * 9 * nf)) != GH_OK) return s;
+    if ((s = dalloc(c, m.evf64, sizeof(double) * 9 * nf)) != GH_OK) return s;
+    if ((s = dalloc(c, m.evf32, sizeof(float) * 9 * nf)) != GH_OK) return s;
+    if ((s = dalloc(c, m.elen, sizeof(double) * ne)) != GH_OK) return s;
+    if ((s = dalloc(c, cot, sizeof(double) * 3 * nf)) != GH_OK) return s;
+    k_face_geom_len<<<blocks_for(nf, T), T, 0, st>>>(ptr<int32_t>(m.F), L, nf, ptr<double>(m.Af), ptr<float>(m.Aff),
+                                                    ptr<double>(cot), ptr<float>(m.gradop), ptr<double>(m.gradop64),
+                                                    ptr<double>(m.evf64), ptr<float>(m.evf32)); ++c->launches;
+    k_edge_geom_len<<<blocks_for(ne, T), T, 0, st>>>(ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
+                                                    ptr<double>(cot), L, ptr<double>(m.theta), ptr<float>(m.ev),
+                                                    ptr<double>(m.elen)); ++c->launches;
+    k_vertex_area<<<blocks_for(nv, T), T, 0, st>>>(ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col_edge), nv,
+                                                  ptr<int32_t>(m.edge_face), ptr<double>(m.Af), ptr<double>(m.Av)); ++c->launches;
+    dfree(c, cot);
+    if ((s = det_mean(c, ptr<double>(m.elen), ne, &m.hbar)) != GH_OK) return s;
+    return check_status(c, "intrinsic geometry");
 }
 
 }  // namespace gh

@@ -19,20 +19,32 @@ template <> __device__ __forceinline__ float sqrt_t<float>(float x) { return sqr
 template <> __device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt(x); }
 
 // Geometry accessors: FP32 stages read the rounded per-face / per-edge
-// operators; FP64 stages recompute them from the FP64 positions.
+// operators; FP64 stages recompute them from the FP64 positions.  On an
+// intrinsic triangulation (evf set) the gradients and the slot edge vectors
+// are each face's own-frame ones, stored per face.
 template <class T> struct Geo;
 template <> struct Geo<float> {
-    const float *gradop, *ev, *Af;
+    const float *gradop, *ev, *Af, *evf;
     __device__ void grad(int64_t f, int k, float *g) const {
         g[0] = gradop[9 * f + 3 * k]; g[1] = gradop[9 * f + 3 * k + 1]; g[2] = gradop[9 * f + 3 * k + 2];
     }
     __device__ void edge(int64_t e, float *v) const { v[0] = ev[3 * e]; v[1] = ev[3 * e + 1]; v[2] = ev[3 * e + 2]; }
+    // the vector of face f's slot k (edge e), lower -> higher vertex
+    __device__ void slot_edge(int64_t f, int k, int64_t e, float *v) const {
+        if (evf) { v[0] = evf[9 * f + 3 * k]; v[1] = evf[9 * f + 3 * k + 1]; v[2] = evf[9 * f + 3 * k + 2]; }
+        else edge(e, v);
+    }
     __device__ float area(int64_t f) const { return Af[f]; }
 };
 template <> struct Geo<double> {
     const double *P, *Af;
     const int32_t *F, *edges;
+    const double *gradop64, *evf;
     __device__ void grad(int64_t f, int k, double *g) const {
+        if (gradop64) {
+            g[0] = gradop64[9 * f + 3 * k]; g[1] = gradop64[9 * f + 3 * k + 1]; g[2] = gradop64[9 * f + 3 * k + 2];
+            return;
+        }
         const double *a = P + 3 * F[3 * f], *b = P + 3 * F[3 * f + 1], *c = P + 3 * F[3 * f + 2];
         double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
         double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
@@ -48,15 +60,21 @@ template <> struct Geo<double> {
         const double *a = P + 3 * edges[2 * e], *b = P + 3 * edges[2 * e + 1];
         v[0] = b[0] - a[0]; v[1] = b[1] - a[1]; v[2] = b[2] - a[2];
     }
+    __device__ void slot_edge(int64_t f, int k, int64_t e, double *v) const {
+        if (evf) { v[0] = evf[9 * f + 3 * k]; v[1] = evf[9 * f + 3 * k + 1]; v[2] = evf[9 * f + 3 * k + 2]; }
+        else edge(e, v);
+    }
     __device__ double area(int64_t f) const { return Af[f]; }
 };
 
 template <class T> Geo<T> make_geo(const DevMesh &m);
 template <> Geo<float> make_geo<float>(const DevMesh &m) {
-    return Geo<float>{ptr<float>(m.gradop), ptr<float>(m.ev), ptr<float>(m.Aff)};
+    return Geo<float>{ptr<float>(m.gradop), ptr<float>(m.ev), ptr<float>(m.Aff),
+                      m.intrinsic ? ptr<float>(m.evf32) : nullptr};
 }
 template <> Geo<double> make_geo<double>(const DevMesh &m) {
-    return Geo<double>{ptr<double>(m.P), ptr<double>(m.Af), ptr<int32_t>(m.F), ptr<int32_t>(m.edges)};
+    return Geo<double>{ptr<double>(m.P), ptr<double>(m.Af), ptr<int32_t>(m.F), ptr<int32_t>(m.edges),
+                       m.intrinsic ? ptr<double>(m.gradop64) : nullptr, m.intrinsic ? ptr<double>(m.evf64) : nullptr};
 }
 
 // ------------------------------------------------------------------ normalise
@@ -260,7 +278,7 @@ __global__ void k_edge_targets(int64_t nf, const int32_t *__restrict__ face_edge
     if (f >= nf) return;
     for (int k = 0; k < 3; ++k) {
         T ev[3];
-        geo.edge(face_edge[3 * f + k], ev);
+        geo.slot_edge(f, k, face_edge[3 * f + k], ev);
         T zz = h[3 * f] * ev[0] + h[3 * f + 1] * ev[1] + h[3 * f + 2] * ev[2];
         z[3 * f + k] = zz;
         w[3 * f + k] = zz;

@@ -1,0 +1,114 @@
+"""The intrinsic Delaunay triangulation (Sec. 5.3) on the GPU against the FP64
+oracle: the triangulation (as a set of triangles) and its edges bit-exact,
+lengths, cotangent weights and vertex areas to 1e-12, the edge-form distances
+within the contract; the face form and a second pass are refused."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from oracle import idt
+
+pytestmark = pytest.mark.gpu
+
+D_TOL = {False: 1e-4, True: 1e-9}
+
+
+@pytest.fixture(scope="module")
+def gh():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_06060_gb300 import build
+    build.build()
+    import paper_1812_06060_gb300 as g
+    g.load_library()
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(gh):
+    c = gh.Context(0)
+    yield c
+    c.close()
+
+
+def _stretched_grid():
+    m = meshgen.jittered_grid(33, 5)
+    m.V[:, 0] *= 3.0
+    m.name = "stretched grid33"
+    return m
+
+
+def _ellipsoid():
+    m = meshgen.noisy_icosphere(4, 2)
+    m.V[:, 0] *= 3.0
+    m.name = "ellipsoid ico4"
+    return m
+
+
+def _d_err(d, dref, sources, hbar):
+    mask = np.isfinite(dref)
+    mask[np.asarray(sources)] = False
+    return np.max(np.abs(d[mask] - dref[mask]) / np.maximum(np.abs(dref[mask]), hbar))
+
+
+def _log(line):
+    import os
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(d):
+        with open(os.path.join(d, "parity_errors.txt"), "a") as f:
+            f.write(line + "\n")
+
+
+@pytest.mark.parametrize("make,src,sweeps", [(_stretched_grid, [40, 700], 300), (_ellipsoid, [0, 1500], 200)],
+                         ids=["grid", "ellipsoid"])
+def test_idt_matches_oracle(gh, ctx, make, src, sweeps):
+    mesh = make()
+    Fi, L, flips_o = idt.intrinsic_delaunay(mesh.V, mesh.F)
+    md = idt.mesh_data_intrinsic(Fi, L, mesh.nv)
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    try:
+        flips = M.intrinsic_delaunay()
+        assert flips > 0
+        Fg = M.dump(gh.GH_DUMP_FACES).reshape(-1, 3)
+        assert set(map(tuple, np.sort(Fg, 1).tolist())) == set(map(tuple, np.sort(Fi, 1).tolist()))
+        assert np.array_equal(M.dump(gh.GH_DUMP_EDGES).reshape(-1, 2), md.edges)
+        for what, ref in ((gh.GH_DUMP_ELEN, md.elen), (gh.GH_DUMP_THETA, md.theta), (gh.GH_DUMP_AV, md.Av)):
+            got = M.dump(what)
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), what
+        ref = idt.solve_intrinsic(md, src, sweeps=sweeps)
+        for fp64 in (True, False):
+            d = np.empty(mesh.nv)
+            M.solve(src, d, gh.params(gs_sweeps=sweeps, form="edge", fp64=fp64))
+            assert np.array_equal(M.dump(gh.GH_DUMP_ORDER), ref["bfs"].order)
+            derr = _d_err(d, ref["d"], src, md.hbar)
+            _log(f"intrinsic Delaunay {mesh.name} flips gpu {flips} / oracle {flips_o} fp64={fp64}: d {derr:.2e}")
+            assert derr <= D_TOL[fp64]
+        with pytest.raises(gh.GeoheatError):
+            M.solve(src, np.empty(mesh.nv), gh.params(gs_sweeps=10, form="face"))
+        with pytest.raises(gh.GeoheatError):
+            M.intrinsic_delaunay()
+    finally:
+        M.close()
+
+
+def test_idt_improves_accuracy_on_a_stretched_grid(gh, ctx):
+    """The planar case has the Euclidean distance as ground truth; the iDT
+    retains accuracy on a poorly triangulated mesh (Sec. 5.3's experiment)."""
+    m = meshgen.jittered_grid(65, 9)
+    m.V[:, 0] *= 4.0
+    src = [2100]
+    exact = np.linalg.norm(m.V - m.V[src[0]], axis=1)
+    mask = exact > 0
+    errs = []
+    for intrinsic in (False, True):
+        M = gh.Mesh(ctx, m.V, m.F)
+        if intrinsic:
+            M.intrinsic_delaunay()
+        d = np.empty(m.nv)
+        M.solve(src, d, gh.params(gs_sweeps=600, form="edge"))
+        errs.append(float(np.mean(np.abs(d[mask] - exact[mask]) / exact[mask])))
+        M.close()
+    _log(f"intrinsic Delaunay stretched grid65 mean rel err vs Euclidean: original {errs[0]:.4f} iDT {errs[1]:.4f}")
+    assert errs[1] < errs[0]
