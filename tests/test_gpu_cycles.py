@@ -52,9 +52,9 @@ def _constraint_values(pc, var, form):
 
 def _log(line):
     import os
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(d):
-        with open(os.path.join(d, "parity_errors.txt"), "a") as f:
+    path = os.environ.get("GEOHEAT_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
             f.write(line + "\n")
 
 

@@ -116,12 +116,11 @@ def _h_err(h, href):
 
 
 def _log(line):
-    """Measured errors, appended to gpurun_out/parity_errors.txt when that
-    folder exists (the GPU runs bring it back)."""
+    """Measured errors, appended to the file GEOHEAT_PARITY_LOG names, if set."""
     import os
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(d):
-        with open(os.path.join(d, "parity_errors.txt"), "a") as f:
+    path = os.environ.get("GEOHEAT_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
             f.write(line + "\n")
 
 
