@@ -78,12 +78,13 @@ def _declare(L):
     L.orc_normalize.restype = C.c_int
     L.orc_normalize.argtypes = [I64, P, I64, P, P, P, P]
     L.orc_face_admm.restype = C.c_int
-    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P, P, P]
+    L.orc_face_admm.argtypes = [I64, P, I64, I64, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P, P, P,
+                                P]
     L.orc_edge_admm.restype = C.c_int
     L.orc_edge_admm.argtypes = [I64, P, I64, P, I64, P, P, P, P, P, P, P, I32, D, D, D, I32, I32, P, P, P, P, P, P,
                                 P, P, P, P]
     L.orc_integrate_face.restype = C.c_int
-    L.orc_integrate_face.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
+    L.orc_integrate_face.argtypes = [I64, P, P, P, P, P, P, P, P, P, I32, P, P, P]
     L.orc_integrate_edge.restype = C.c_int
     L.orc_integrate_edge.argtypes = [I64, P, P, P, P, P, P, P, I32, P, P, P]
 
@@ -230,15 +231,17 @@ def normalize(md: MeshData, state) -> np.ndarray:
     return h
 
 
-def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
+def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None, eslot=None):
     """Face-based ADMM (Sec. 3.2).  Returns g [nf,3], y [nf,3,3],
     lambda [nf,3,3] (NaN on boundary slots) and residuals [iterations run, 3]
     (|r_primal|, |r_dual|, |M|_F).  eps = (eps1, eps2) stops once both
     residuals are within |M|_F * eps (Sec. 3.2); None runs all iters.
     pc = path_constraints(md, sources, "face") adds the multi-source
-    constraints of Sec. 5.2."""
+    constraints of Sec. 5.2.  eslot [nf,3,3]: an intrinsic triangulation's
+    slot edge vectors in each face's own frame (Sec. 5.3)."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     npc, off, var, coef = _pc_args(pc, 3)
+    es = None if eslot is None else np.ascontiguousarray(eslot, dtype=np.float64)
     g = np.empty((md.nf, 3))
     y = np.empty((md.nf, 3, 3))
     lam = np.empty((md.nf, 3, 3))
@@ -247,7 +250,7 @@ def face_admm(md: MeshData, h, iters=ADMM_ITERS, mu=MU, eps=None, pc=None):
     e1, e2 = eps if eps is not None else (0.0, 0.0)
     _check(lib().orc_face_admm(md.nv, _p(md.P), md.nf, md.ne, _p(md.edges), _p(md.face_edge), _p(md.edge_face),
                                _p(md.edge_slot), _p(md.Af), _p(h), iters, mu, e1, e2, int(eps is not None), npc,
-                               _p(off), _p(var), _p(coef), _p(g), _p(y), _p(lam), _p(res), C.byref(done)),
+                               _p(off), _p(var), _p(coef), _p(es), _p(g), _p(y), _p(lam), _p(res), C.byref(done)),
            "orc_face_admm")
     return g, y, lam, res[:done.value]
 
@@ -540,14 +543,16 @@ def _pc_args(pc, dim):
     return len(pc.off) - 1, np.ascontiguousarray(pc.off), np.ascontiguousarray(var), coef
 
 
-def integrate_face(md: MeshData, b: BFS, g, parent=None) -> np.ndarray:
-    """Breadth-first integration of face gradients (eq. IntegrationStep)."""
+def integrate_face(md: MeshData, b: BFS, g, parent=None, eslot=None) -> np.ndarray:
+    """Breadth-first integration of face gradients (eq. IntegrationStep);
+    eslot as for face_admm on an intrinsic triangulation."""
     g = np.ascontiguousarray(g, dtype=np.float64)
+    es = None if eslot is None else np.ascontiguousarray(eslot, dtype=np.float64)
     par = np.ascontiguousarray(b.parent if parent is None else parent, dtype=np.int32)
     d = np.empty(md.nv)
     _check(lib().orc_integrate_face(md.nv, _p(md.P), _p(md.rowptr), _p(md.col), _p(md.col_edge),
-                                    _p(md.edge_face), _p(b.order), _p(b.level_off), b.nlev, _p(par), _p(g),
-                                    _p(d)), "orc_integrate_face")
+                                    _p(md.edge_face), _p(md.edge_slot), _p(es), _p(b.order), _p(b.level_off),
+                                    b.nlev, _p(par), _p(g), _p(d)), "orc_integrate_face")
     return d
 
 

@@ -578,7 +578,7 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
                   const int32_t *face_edge, const int32_t *edge_face, const int32_t *edge_slot, const double *Af,
                   const double *h, int32_t iters, double mu, double eps1, double eps2, int32_t early_stop,
                   int32_t npc, const int32_t *pc_off, const int32_t *pc_var, const double *pc_coef,
-                  double *g, double *y, double *lam, double *res, int32_t *done) {
+                  const double *eslot, double *g, double *y, double *lam, double *res, int32_t *done) {
     (void)nv;
     if (npc < 0 || npc > 64) return ORC_EINVAL;
     orc_pc pc;
@@ -617,15 +617,30 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
             int k1 = edge_slot[2 * e], k2 = edge_slot[2 * e + 1];
             double A1 = Af[f1], A2 = Af[f2];
             double a1 = sqrt(A1), a2 = sqrt(A2);
-            double ev[3];
-            sub3(P + 3 * edges[2 * e + 1], P + 3 * edges[2 * e], ev);
-            double el = norm3(ev);
-            double eb[3] = {ev[0] / el, ev[1] / el, ev[2] / el};
             double q1[3], q2[3];
             for (int c = 0; c < 3; ++c) {
                 q1[c] = g[3 * f1 + c] - lam[9 * f1 + 3 * k1 + c] / (mu * a1);
                 q2[c] = g[3 * f2 + c] - lam[9 * f2 + 3 * k2 + c] / (mu * a2);
             }
+            if (eslot) {
+                /* an intrinsic triangulation (Sec. 5.3): each face has its own
+                 * frame and its own unit vector e_i of the edge; the condition
+                 * e_1 . y_1 = e_2 . y_2 gives y_1 = q_1 + A2/(A1+A2) e_1 p,
+                 * y_2 = q_2 - A1/(A1+A2) e_2 p, p = e_2 . q_2 - e_1 . q_1 */
+                const double *v1 = eslot + 9 * f1 + 3 * k1, *v2 = eslot + 9 * f2 + 3 * k2;
+                double n1 = norm3(v1), n2 = norm3(v2);
+                double e1[3] = {v1[0] / n1, v1[1] / n1, v1[2] / n1}, e2[3] = {v2[0] / n2, v2[1] / n2, v2[2] / n2};
+                double proj = dot3(e2, q2) - dot3(e1, q1);
+                for (int c = 0; c < 3; ++c) {
+                    y[9 * f1 + 3 * k1 + c] = q1[c] + A2 / (A1 + A2) * e1[c] * proj;
+                    y[9 * f2 + 3 * k2 + c] = q2[c] - A1 / (A1 + A2) * e2[c] * proj;
+                }
+                continue;
+            }
+            double ev[3];
+            sub3(P + 3 * edges[2 * e + 1], P + 3 * edges[2 * e], ev);
+            double el = norm3(ev);
+            double eb[3] = {ev[0] / el, ev[1] / el, ev[2] / el};
             double dq[3] = {q2[0] - q1[0], q2[1] - q1[1], q2[2] - q1[2]};
             double proj = dot3(eb, dq);
             for (int c = 0; c < 3; ++c) {
@@ -805,11 +820,14 @@ static int32_t csr_edge(const int32_t *rowptr, const int32_t *col, const int32_t
  * pairing vertex v_k = parent[j] in D_{i-1}:
  *   d(v_j) = d(v_k) + 1/|T_jk| sum_{f in T_jk} g_f . (p_j - p_k)
  * where T_jk are the faces that contain both vertices.  Sources keep d = 0
- * (Sec. 5.2); unreachable vertices get +infinity.
+ * (Sec. 5.2); unreachable vertices get +infinity.  eslot (nullable): an
+ * intrinsic triangulation's slot edge vectors in each face's own frame
+ * (lower -> higher vertex), which give p_j - p_k there (Sec. 5.3).
  */
 int orc_integrate_face(int64_t nv, const double *P, const int32_t *rowptr, const int32_t *col,
-                       const int32_t *col_edge, const int32_t *edge_face, const int32_t *order,
-                       const int32_t *level_off, int32_t nlev, const int32_t *parent, const double *g, double *d) {
+                       const int32_t *col_edge, const int32_t *edge_face, const int32_t *edge_slot,
+                       const double *eslot, const int32_t *order, const int32_t *level_off, int32_t nlev,
+                       const int32_t *parent, const double *g, double *d) {
     for (int64_t v = 0; v < nv; ++v) d[v] = INFINITY;
     for (int32_t q = level_off[0]; q < level_off[1]; ++q) d[order[q]] = 0.0;
     for (int32_t i = 1; i < nlev; ++i) {
@@ -824,6 +842,11 @@ int orc_integrate_face(int64_t nv, const double *P, const int32_t *rowptr, const
             for (int a = 0; a < 2; ++a) {
                 int32_t f = edge_face[2 * e + a];
                 if (f < 0) continue;
+                if (eslot) {   /* p_j - p_k in face f's own frame: its slot vector, lower -> higher */
+                    const double *v = eslot + 9 * f + 3 * edge_slot[2 * e + a];
+                    const double sg = (j > k) ? 1.0 : -1.0;
+                    dp[0] = sg * v[0]; dp[1] = sg * v[1]; dp[2] = sg * v[2];
+                }
                 s += dot3(g + 3 * f, dp);
                 ++n;
             }

@@ -20,8 +20,14 @@ READINGS:
 - on the iDT the diffusion uses cotangents and vertex areas from the
   lengths; normalisation and the edge form's target differences use each
   face's own frame (corner 0 at the origin, corner 1 on the +x axis, corner 2
-  above it); only the edge form runs on it (Sec. 5.3 gives the face form no
-  closed form).
+  above it);
+- the face form on the iDT (Sec. 5.3 leaves its derivation to the reader):
+  g, y and lambda live in each face's frame, and the compatibility condition
+  of an edge compares each face's projection on its own unit vector of the
+  edge, e_1 . g_1 = e_2 . g_2, so the Y-update becomes
+  y_1 = q_1 + A2/(A1+A2) e_1 p, y_2 = q_2 - A1/(A1+A2) e_2 p with
+  p = e_2 . q_2 - e_1 . q_1 (the 3D update when e_1 = e_2); the integration
+  takes p_j - p_k in each face's frame.
 """
 from __future__ import annotations
 
@@ -30,7 +36,8 @@ from collections import deque
 
 import numpy as np
 
-from . import (ADMM_ITERS, MU, MeshData, _check, _p, bfs, diffusion_time, edge_admm, gs, integrate_edge, lib)
+from . import (ADMM_ITERS, MU, MeshData, _check, _p, bfs, diffusion_time, edge_admm, face_admm, gs,
+               integrate_edge, integrate_face, lib)
 
 IDT_TOL = 1e-12
 
@@ -215,6 +222,20 @@ def normalize_intrinsic(md: MeshData, state) -> np.ndarray:
     return h
 
 
+def slot_vectors(md: MeshData) -> np.ndarray:
+    """[nf,3,3]: the edge opposite corner k in face f's frame, from its lower
+    to its higher vertex (third component 0)"""
+    S = np.zeros((md.nf, 3, 3))
+    for f in range(md.nf):
+        q = md.frame[f]
+        vs = md.F[f]
+        for k in range(3):
+            i, j = (k + 1) % 3, (k + 2) % 3
+            tail, head = (i, j) if vs[i] < vs[j] else (j, i)
+            S[f, k, :2] = q[head] - q[tail]
+    return S
+
+
 def edge_targets_intrinsic(md: MeshData, h) -> np.ndarray:
     """z[f,k] = h_f . (q_head - q_tail) in the face's frame, for the edge
     opposite corner k oriented from its lower to its higher vertex
@@ -231,15 +252,24 @@ def edge_targets_intrinsic(md: MeshData, h) -> np.ndarray:
 
 
 def solve_intrinsic(md: MeshData, sources, sweeps: int = 200, m: float = 1.0, t: float | None = None,
-                    admm_iters: int = ADMM_ITERS, mu: float = MU) -> dict:
-    """The edge-form path on an intrinsic triangulation (Sec. 5.3)."""
+                    admm_iters: int = ADMM_ITERS, mu: float = MU, form: str = "edge") -> dict:
+    """Algorithm 1 on an intrinsic triangulation (Sec. 5.3), edge or face form."""
     t = diffusion_time(md, m) if t is None else t
     b = bfs(md, sources)
     st = gs(md, b, t, sweeps)
     h = normalize_intrinsic(md, st)
-    z = edge_targets_intrinsic(md, h)
-    x, w, lam, z2, res = edge_admm(md, h, admm_iters, mu, z_in=z)
-    return {"t": t, "bfs": b, "u": st, "h": h, "z": z2, "x": x, "res": res, "d": integrate_edge(md, b, x)}
+    out = {"t": t, "bfs": b, "u": st, "h": h}
+    if form == "edge":
+        z = edge_targets_intrinsic(md, h)
+        x, w, lam, z2, res = edge_admm(md, h, admm_iters, mu, z_in=z)
+        out.update(z=z2, x=x, res=res, d=integrate_edge(md, b, x))
+    elif form == "face":
+        S = slot_vectors(md)
+        g, y, lam, res = face_admm(md, h, admm_iters, mu, eslot=S)
+        out.update(g=g, res=res, d=integrate_face(md, b, g, eslot=S))
+    else:
+        raise ValueError(form)
+    return out
 
 
 def quality(V_or_none, F, L) -> float:

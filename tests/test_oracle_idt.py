@@ -77,3 +77,29 @@ def test_curved_mesh_ends_delaunay_area_kept_second_pass_idle():
     assert s.min() >= -idt.IDT_TOL
     F2, L2, flips2 = idt.intrinsic_delaunay(None, Fi, L)
     assert flips2 == 0 and np.array_equal(F2, Fi)
+
+
+def test_intrinsic_face_form_is_the_face_form_on_the_triangulation(planar):
+    """on a planar mesh the frames only rotate g: the face-form distances of
+    the intrinsic formulation are those of the ordinary one"""
+    m, V, Fi, L, _ = planar
+    mi = idt.mesh_data_intrinsic(Fi, L, len(V))
+    me = oracle.mesh_data(V, Fi)
+    src = [40, 200]
+    ri = idt.solve_intrinsic(mi, src, sweeps=150, form="face")
+    re = oracle.solve(me, src, "face", sweeps=150)
+    fin = np.isfinite(re["d"])
+    assert np.abs(ri["d"][fin] - re["d"][fin]).max() <= 1e-12 * np.abs(re["d"][fin]).max()
+    assert np.allclose(np.linalg.norm(ri["g"], axis=1), np.linalg.norm(re["g"], axis=1), rtol=0, atol=1e-12)
+    assert np.allclose(ri["res"], re["res"], rtol=1e-10, atol=1e-14)
+
+
+def test_intrinsic_face_form_on_an_ellipsoid_ends_close_to_the_edge_form():
+    m = meshgen.noisy_icosphere(3, 2)
+    m.V[:, 0] *= 3.0
+    Fi, L, _ = idt.intrinsic_delaunay(m.V, m.F)
+    mi = idt.mesh_data_intrinsic(Fi, L, m.nv)
+    rf = idt.solve_intrinsic(mi, [0], sweeps=200, form="face", admm_iters=200)
+    re = idt.solve_intrinsic(mi, [0], sweeps=200, form="edge", admm_iters=200)
+    fin = np.isfinite(re["d"]) & (re["d"] > 0)
+    assert np.max(np.abs(rf["d"][fin] - re["d"][fin]) / re["d"][fin]) < 0.05
