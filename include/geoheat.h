@@ -192,9 +192,11 @@ gh_status gh_mesh_set_tuning(gh_mesh mesh, int32_t kind, int32_t bfs_cluster);
  * triangles unfolded into the plane) until none is left.  A flip that would
  * join two vertices already joined is left out.  Afterwards the mesh is the
  * face list plus edge lengths: the diffusion uses cotangents and vertex areas
- * from the lengths, normalisation and the edge form's target differences use
- * each face's own frame, and only the edge form solves on it (GH_EINVAL for
- * the face form).  The vertices and their indices are unchanged; faces and
+ * from the lengths, normalisation, the edge form's target differences and
+ * the face form's gradients use each face's own frame (in the face form an
+ * edge's compatibility compares each face's projection on its own unit
+ * vector of the edge), and the constraints of Sec. 5 run in the edge form
+ * only (GH_EINVAL otherwise).  The vertices and their indices are unchanged; faces and
  * edges are those of the new triangulation (GH_DUMP_FACES, GH_DUMP_EDGES,
  * GH_DUMP_ELEN).  flips (nullable) receives the number of flips.
  * GH_EINVAL if the mesh is already intrinsic, GH_EBUSY while serving

@@ -17,14 +17,18 @@ template <class T> struct alignas(4 * sizeof(T)) Quad { T x, y, z, w; };
 //   y_k = q_k + A'/(A + A') ebar (ebar . (q'_k - q_k))   (q' of the twin slot)
 //   gn  = (2h + mu sum_k (y_k + g - q_k)) / (2 + mu n)
 // over the n interior slots.  rec is the per-face record (unit edge vectors
-// with twin weights A'/(A + A'), sqrt(A_f)).
+// with twin weights A'/(A + A'), sqrt(A_f)).  INTR: an intrinsic
+// triangulation (Sec. 5.3), where every face has its own frame and its own
+// unit vector e of each edge; the condition e . y = e' . y' then gives
+// y_k = q_k + A'/(A + A') e (e' . q'_k - e . q_k), the twin's e' read from
+// the twin's record (the same update when e = e').
 template <class T> struct FaceIter {
     T g[3], q[3][3], y[3][3], gn[3];
     bool in[3];
     T alpha;
 };
 
-template <class T>
+template <class T, bool INTR = false>
 __device__ __forceinline__ void face_update(int64_t f, const int32_t *__restrict__ twin, const T *__restrict__ rec,
                                             const T *__restrict__ h, const T *__restrict__ g_in,
                                             const T *__restrict__ q_in, T mu, int first, FaceIter<T> &s) {
@@ -43,7 +47,14 @@ __device__ __forceinline__ void face_update(int64_t f, const int32_t *__restrict
         if (!s.in[k]) continue;
         const T *qt = first ? h + 3 * (int64_t)(tw >> 2) : q_in + 9 * (int64_t)(tw >> 2) + 3 * (tw & 3);
         const T eb[3] = {ek[k].x, ek[k].y, ek[k].z};
-        const T proj = eb[0] * (qt[0] - s.q[k][0]) + eb[1] * (qt[1] - s.q[k][1]) + eb[2] * (qt[2] - s.q[k][2]);
+        T proj;
+        if (INTR) {
+            const T *et = rec + 16 * (int64_t)(tw >> 2) + 4 * (tw & 3);
+            proj = (et[0] * qt[0] + et[1] * qt[1] + et[2] * qt[2]) -
+                   (eb[0] * s.q[k][0] + eb[1] * s.q[k][1] + eb[2] * s.q[k][2]);
+        } else {
+            proj = eb[0] * (qt[0] - s.q[k][0]) + eb[1] * (qt[1] - s.q[k][1]) + eb[2] * (qt[2] - s.q[k][2]);
+        }
         for (int c = 0; c < 3; ++c) {
             s.y[k][c] = s.q[k][c] + ek[k].w * eb[c] * proj;
             acc[c] += s.y[k][c] + (s.g[c] - s.q[k][c]);

@@ -192,8 +192,8 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
     const int K = (int)items.size();
     gh_status s = GH_OK;
     for (Item &it : items) {
-        if (it.m->intrinsic && it.p->form == GH_FORM_FACE) {
-            set_error("an intrinsic triangulation solves in the edge form only (Sec. 5.3)");
+        if (it.m->intrinsic && it.p->form == GH_FORM_FACE && (it.p->path_constraints || it.p->cycle_constraints)) {
+            set_error("the constraints of Sec. 5 run on an intrinsic triangulation in the edge form only");
             return GH_EINVAL;
         }
         if ((s = ensure_ws(c, *it.m, *it.w, it.p->fp64, it.p->form, it.p->admm_iters)) != GH_OK) return s;

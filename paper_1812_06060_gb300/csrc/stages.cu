@@ -187,15 +187,20 @@ template <class T> __global__ void k_face_final(int64_t n, T *g0, const T *__res
 template <class T>
 __global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32_t *__restrict__ edges,
                            const int32_t *__restrict__ face_edge, const int32_t *__restrict__ twin,
-                           const double *__restrict__ Af, T *rec) {
+                           const double *__restrict__ Af, const double *__restrict__ evf, T *rec) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const double A = Af[f];
     T *o = rec + 16 * f;
     for (int k = 0; k < 3; ++k) {
-        const int e = face_edge[3 * f + k];
-        const double *a = P + 3 * edges[2 * e], *b = P + 3 * edges[2 * e + 1];
-        const double v[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        double v[3];
+        if (evf) {   // an intrinsic triangulation: the slot's vector in the face's own frame
+            for (int c = 0; c < 3; ++c) v[c] = evf[9 * f + 3 * k + c];
+        } else {
+            const int e = face_edge[3 * f + k];
+            const double *a = P + 3 * edges[2 * e], *b = P + 3 * edges[2 * e + 1];
+            for (int c = 0; c < 3; ++c) v[c] = b[c] - a[c];
+        }
         const double il = 1.0 / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         const int tw = twin[3 * f + k];
         const double A2 = (tw >= 0) ? Af[tw >> 2] : 0.0;
@@ -218,8 +223,9 @@ __global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32
 // constraints, g' = gn - delta on the constrained faces (pcm[f] = the face's
 // index in delta, else -1), the correction of the KKT projection.
 // Optional residual partials per block: [0] |alpha (y - g')|^2,
-// [1] |mu alpha (g' - g)|^2 summed over interior slots.
-template <class T>
+// [1] |mu alpha (g' - g)|^2 summed over interior slots.  INTR: an intrinsic
+// triangulation (face_update).
+template <class T, bool INTR>
 __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__restrict__ twin,
                                                   const T *__restrict__ rec, const T *__restrict__ h,
                                                   const T *__restrict__ g_in, const T *__restrict__ q_in, T *g_out,
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
     double rp = 0.0, rd = 0.0;
     if (f < nf) {
         FaceIter<T> s;
-        face_update(f, twin, rec, h, g_in, q_in, mu, first, s);
+        face_update<T, INTR>(f, twin, rec, h, g_in, q_in, mu, first, s);
         if (pcm) {
             const int u = pcm[f];
             if (u >= 0)
@@ -479,7 +485,7 @@ __global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, cons
                              const int32_t *__restrict__ pedge, const int32_t *__restrict__ edges,
                              const int32_t *__restrict__ edge_face, const double *__restrict__ P,
                              const T *__restrict__ g, const T *__restrict__ x, int form, double *inc, int32_t *nxt,
-                             double *d) {
+                             double *d, const int32_t *__restrict__ edge_slot, const double *__restrict__ evf) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     int lv = level[v];
@@ -496,12 +502,22 @@ __global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, cons
         double xe = (double)x[e];
         dv = (edges[2 * e + 1] == (int)v) ? xe : -xe;
     } else {
-        double dp[3] = {P[3 * v] - P[3 * p], P[3 * v + 1] - P[3 * p + 1], P[3 * v + 2] - P[3 * p + 2]};
+        double dp[3] = {0.0, 0.0, 0.0};
+        if (!evf) {
+            dp[0] = P[3 * v] - P[3 * p];
+            dp[1] = P[3 * v + 1] - P[3 * p + 1];
+            dp[2] = P[3 * v + 2] - P[3 * p + 2];
+        }
         double s = 0.0;
         int n = 0;
         for (int a = 0; a < 2; ++a) {
             int f = edge_face[2 * e + a];
             if (f < 0) continue;
+            if (evf) {   // an intrinsic triangulation: p_v - p_p in face f's frame, its slot vector
+                const double *sv = evf + 9 * (int64_t)f + 3 * edge_slot[2 * e + a];
+                const double sg = ((int)v > p) ? 1.0 : -1.0;
+                dp[0] = sg * sv[0]; dp[1] = sg * sv[1]; dp[2] = sg * sv[2];
+            }
             s += (double)g[3 * f] * dp[0] + (double)g[3 * f + 1] * dp[1] + (double)g[3 * f + 2] * dp[2];
             ++n;
         }
@@ -586,7 +602,9 @@ template <class T> gh_status face_rec(Ctx *c, DevMesh &m, const T *&out) {
         if (s != GH_OK) return s;
         k_face_rec<T><<<blocks_for(m.nf, NT), NT, 0, c->stream>>>(m.nf, ptr<double>(m.P), ptr<int32_t>(m.edges),
                                                                  ptr<int32_t>(m.face_edge), ptr<int32_t>(m.twin),
-                                                                 ptr<double>(m.Af), ptr<T>(buf)); ++c->launches;
+                                                                 ptr<double>(m.Af),
+                                                                 m.intrinsic ? ptr<double>(m.evf64) : nullptr,
+                                                                 ptr<T>(buf)); ++c->launches;
         GH_CUDA(cudaGetLastError());
         GH_CUDA(cudaStreamSynchronize(c->stream));
     }
@@ -623,9 +641,10 @@ template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int ite
                                                   (T)mu, it == 0, ptr<T>(q.pc_val), ptr<T>(q.pc_delta),
                                                   early ? ctl : nullptr); ++c->launches;
         }
-        k_face_admm<T><<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1],
-                                          qq[a ^ 1], (T)mu, part, early ? ctl : nullptr, it == 0,
-                                          pc ? ptr<int32_t>(q.pc_map) : nullptr, pc ? ptr<T>(q.pc_delta) : nullptr);
+        auto kern = m.intrinsic ? k_face_admm<T, true> : k_face_admm<T, false>;
+        kern<<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1], qq[a ^ 1],
+                                (T)mu, part, early ? ctl : nullptr, it == 0, pc ? ptr<int32_t>(q.pc_map) : nullptr,
+                                pc ? ptr<T>(q.pc_delta) : nullptr);
         ++c->launches;
         if (part) {
             k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it, early ? ctl : nullptr); ++c->launches;
@@ -689,7 +708,8 @@ template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, d
     k_increments<T><<<nb, NT, 0, st>>>(m.nv, ptr<int32_t>(q.level), ptr<int32_t>(q.parent), ptr<int32_t>(q.pedge),
                                        ptr<int32_t>(m.edges),
                                        ptr<int32_t>(m.edge_face), ptr<double>(m.P), ptr<T>(q.g0), ptr<T>(q.x), q.form,
-                                       ptr<double>(q.inc), n[0], d[0]); ++c->launches;
+                                       ptr<double>(q.inc), n[0], d[0], ptr<int32_t>(m.edge_slot),
+                                       m.intrinsic ? ptr<double>(m.evf64) : nullptr); ++c->launches;
     int rounds = 0;
     while ((1 << rounds) < q.nlev) ++rounds;
     int cur = 0;

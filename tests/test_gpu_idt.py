@@ -1,7 +1,8 @@
 """The intrinsic Delaunay triangulation (Sec. 5.3) on the GPU against the FP64
 oracle: the triangulation (as a set of triangles) and its edges bit-exact,
-lengths, cotangent weights and vertex areas to 1e-12, the edge-form distances
-within the contract; the face form and a second pass are refused."""
+lengths, cotangent weights and vertex areas to 1e-12, the distances of both
+forms within the contract; the constraints of Sec. 5 in the face form and a
+second pass are refused."""
 import numpy as np
 import pytest
 
@@ -77,16 +78,18 @@ def test_idt_matches_oracle(gh, ctx, make, src, sweeps):
         for what, ref in ((gh.GH_DUMP_ELEN, md.elen), (gh.GH_DUMP_THETA, md.theta), (gh.GH_DUMP_AV, md.Av)):
             got = M.dump(what)
             assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), what
-        ref = idt.solve_intrinsic(md, src, sweeps=sweeps)
-        for fp64 in (True, False):
-            d = np.empty(mesh.nv)
-            M.solve(src, d, gh.params(gs_sweeps=sweeps, form="edge", fp64=fp64))
-            assert np.array_equal(M.dump(gh.GH_DUMP_ORDER), ref["bfs"].order)
-            derr = _d_err(d, ref["d"], src, md.hbar)
-            _log(f"intrinsic Delaunay {mesh.name} flips gpu {flips} / oracle {flips_o} fp64={fp64}: d {derr:.2e}")
-            assert derr <= D_TOL[fp64]
+        for form in ("edge", "face"):
+            ref = idt.solve_intrinsic(md, src, sweeps=sweeps, form=form)
+            for fp64 in (True, False):
+                d = np.empty(mesh.nv)
+                M.solve(src, d, gh.params(gs_sweeps=sweeps, form=form, fp64=fp64))
+                assert np.array_equal(M.dump(gh.GH_DUMP_ORDER), ref["bfs"].order)
+                derr = _d_err(d, ref["d"], src, md.hbar)
+                _log(f"intrinsic Delaunay {mesh.name} flips gpu {flips} / oracle {flips_o} form={form} "
+                     f"fp64={fp64}: d {derr:.2e}")
+                assert derr <= D_TOL[fp64]
         with pytest.raises(gh.GeoheatError):
-            M.solve(src, np.empty(mesh.nv), gh.params(gs_sweeps=10, form="face"))
+            M.solve(src, np.empty(mesh.nv), gh.params(gs_sweeps=10, form="face", path_constraints=True))
         with pytest.raises(gh.GeoheatError):
             M.intrinsic_delaunay()
     finally:
