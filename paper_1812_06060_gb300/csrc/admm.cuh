@@ -16,8 +16,9 @@ template <class T> struct alignas(4 * sizeof(T)) Quad { T x, y, z, w; };
 //   g = h, lambda = 0, so q_k = h), then
 //   y_k = q_k + A'/(A + A') ebar (ebar . (q'_k - q_k))   (q' of the twin slot)
 //   gn  = (2h + mu sum_k (y_k + g - q_k)) / (2 + mu n)
-// over the n interior slots.  rec is the per-face record (unit edge vectors
-// with twin weights A'/(A + A'), sqrt(A_f)).  INTR: an intrinsic
+// over the n interior slots.  rec holds 12 values per face (per slot the unit
+// edge vector and the twin weight A'/(A + A'); 48 bytes in FP32), then
+// sqrt(A_f) of every face at rec[12 nf + f].  INTR: an intrinsic
 // triangulation (Sec. 5.3), where every face has its own frame and its own
 // unit vector e of each edge; the condition e . y = e' . y' then gives
 // y_k = q_k + A'/(A + A') e (e' . q'_k - e . q_k), the twin's e' read from
@@ -25,16 +26,14 @@ template <class T> struct alignas(4 * sizeof(T)) Quad { T x, y, z, w; };
 template <class T> struct FaceIter {
     T g[3], q[3][3], y[3][3], gn[3];
     bool in[3];
-    T alpha;
 };
 
 template <class T, bool INTR = false>
 __device__ __forceinline__ void face_update(int64_t f, const int32_t *__restrict__ twin, const T *__restrict__ rec,
                                             const T *__restrict__ h, const T *__restrict__ g_in,
                                             const T *__restrict__ q_in, T mu, int first, FaceIter<T> &s) {
-    const Quad<T> *r4 = reinterpret_cast<const Quad<T> *>(rec + 16 * f);
+    const Quad<T> *r4 = reinterpret_cast<const Quad<T> *>(rec + 12 * f);
     const Quad<T> ek[3] = {r4[0], r4[1], r4[2]};
-    s.alpha = r4[3].x;
     const T *gsrc = first ? h : g_in;
     for (int c = 0; c < 3; ++c) s.g[c] = gsrc[3 * f + c];
     T acc[3] = {0, 0, 0};
@@ -49,7 +48,7 @@ __device__ __forceinline__ void face_update(int64_t f, const int32_t *__restrict
         const T eb[3] = {ek[k].x, ek[k].y, ek[k].z};
         T proj;
         if (INTR) {
-            const T *et = rec + 16 * (int64_t)(tw >> 2) + 4 * (tw & 3);
+            const T *et = rec + 12 * (int64_t)(tw >> 2) + 4 * (tw & 3);
             proj = (et[0] * qt[0] + et[1] * qt[1] + et[2] * qt[2]) -
                    (eb[0] * s.q[k][0] + eb[1] * s.q[k][1] + eb[2] * s.q[k][2]);
         } else {

@@ -31,7 +31,7 @@ struct BfsArgs {
     int32_t *parent;
     int32_t *pedge;
     int32_t *order;
-    int32_t *rb, *re;       // row bounds of each queue entry, recorded when its keys are offered (scratch)
+    int32_t *rb, *re;       // row bounds of each queue entry, recorded when it is placed (scratch)
     unsigned long long *key;
     int32_t *lvl_off;
     int32_t *meta;
@@ -135,31 +135,42 @@ __device__ __forceinline__ void bfs_offer(const BfsArgs &a, int r, int b, int fr
     }
 }
 
+// writes one child w (pairing vertex p, pairing edge ce) at queue position
+// at, with its row bounds (loaded here, in the round trip of the edge id)
+__device__ __forceinline__ void bfs_put(const BfsArgs &a, int nlev, int p, int w, int ce, int rb, int re, int at) {
+    a.order[at] = w;
+    a.rb[at] = rb;
+    a.re[at] = re;
+    a.level[w] = nlev;
+    a.parent[w] = p;
+    a.pedge[w] = ce;
+}
+
 // writes the children of parent p (rank r, row [b, e)) among slots [from, e)
 // from queue position at on; returns the next position
 __device__ __forceinline__ int bfs_place(const BfsArgs &a, int nlev, int p, int r, int b, int from, int e,
                                          unsigned mk, int at) {
     for (int j0 = from; j0 < e; j0 += kSlotBatch) {
-        int w[kSlotBatch], ce[kSlotBatch];
+        int w[kSlotBatch];
         bool ch[kSlotBatch];
 #pragma unroll
-        for (int u = 0; u < kSlotBatch; ++u) {
-            const bool in = j0 + u < e;
-            w[u] = in ? __ldg(&a.col[j0 + u]) : -1;
-            ce[u] = in ? __ldg(&a.col_edge[j0 + u]) : -1;
-        }
+        for (int u = 0; u < kSlotBatch; ++u) w[u] = j0 + u < e ? __ldg(&a.col[j0 + u]) : -1;
 #pragma unroll
         for (int u = 0; u < kSlotBatch; ++u) {
             const int sl = j0 + u - b;
             ch[u] = w[u] >= 0 && (sl < 32 ? ((mk >> sl) & 1u) != 0 : __ldcg(&a.key[w[u]]) == bfs_key(r, sl));
         }
+        int ce[kSlotBatch], cb[kSlotBatch], cx[kSlotBatch];   // all loads first: one round trip
+#pragma unroll
+        for (int u = 0; u < kSlotBatch; ++u) {
+            ce[u] = ch[u] ? __ldg(&a.col_edge[j0 + u]) : 0;
+            cb[u] = ch[u] ? __ldg(&a.rowptr[w[u]]) : 0;
+            cx[u] = ch[u] ? __ldg(&a.rowptr[w[u] + 1]) : 0;
+        }
 #pragma unroll
         for (int u = 0; u < kSlotBatch; ++u) {
             if (ch[u]) {
-                a.order[at] = w[u];
-                a.level[w[u]] = nlev;
-                a.parent[w[u]] = p;
-                a.pedge[w[u]] = ce[u];
+                bfs_put(a, nlev, p, w[u], ce[u], cb[u], cx[u], at);
                 ++at;
             }
         }
@@ -176,13 +187,12 @@ struct Held {
     int w[kSlotBatch];
 };
 
-// row bounds and offers of rank r; the first slots are kept in h
+// offers of rank r (its row bounds recorded at placement); the first slots
+// are kept in h
 __device__ __forceinline__ void bfs_offer_held(const BfsArgs &a, int r, Held &h) {
     h.v = __ldcg(&a.order[r]);
-    h.b = a.rowptr[h.v];
-    h.e = a.rowptr[h.v + 1];
-    a.rb[r] = h.b;
-    a.re[r] = h.e;
+    h.b = __ldcg(&a.rb[r]);
+    h.e = __ldcg(&a.re[r]);
 #pragma unroll
     for (int u = 0; u < kSlotBatch; ++u) h.w[u] = h.b + u < h.e ? __ldg(&a.col[h.b + u]) : -1;
 #pragma unroll
@@ -199,10 +209,7 @@ __device__ __forceinline__ void bfs_offer_set(const BfsArgs &a, int plo, int phi
     for (int u = 0; u < kSlotBatch; ++u) h.w[u] = -1;
     if (plo + (int)threadIdx.x < phi) bfs_offer_held(a, plo + (int)threadIdx.x, h);
     for (int r = plo + (int)threadIdx.x + BT; r < phi; r += BT) {
-        const int v = __ldcg(&a.order[r]);
-        const int b = a.rowptr[v], e = a.rowptr[v + 1];
-        a.rb[r] = b;
-        a.re[r] = e;
+        const int b = __ldcg(&a.rb[r]), e = __ldcg(&a.re[r]);
         bfs_offer(a, r, b, b, e);
     }
 }
@@ -226,6 +233,12 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         const int per = (a.n0 + CL - 1) / CL;
         plo = min(a.n0, crank * per);
         phi = min(a.n0, plo + per);
+        for (int r = plo + (int)threadIdx.x; r < phi; r += BT) {
+            const int v = a.order[r];
+            a.rb[r] = a.rowptr[v];
+            a.re[r] = a.rowptr[v + 1];
+        }
+        __syncthreads();
         bfs_offer_set(a, plo, phi, h);
     }
     cluster.sync();
@@ -287,16 +300,18 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         // CTA's earlier chunks) + (earlier parents of the chunk)
         if (k0) {
             int at = hi + before + ex0;
-            int ce[kSlotBatch];
+            int ce[kSlotBatch], cb[kSlotBatch], cx[kSlotBatch];   // all loads first: one round trip
 #pragma unroll
-            for (int u = 0; u < kSlotBatch; ++u) ce[u] = h.w[u] >= 0 ? __ldg(&a.col_edge[h.b + u]) : -1;
+            for (int u = 0; u < kSlotBatch; ++u) {
+                const bool ch = h.w[u] >= 0;
+                ce[u] = ch ? __ldg(&a.col_edge[h.b + u]) : 0;
+                cb[u] = ch ? __ldg(&a.rowptr[h.w[u]]) : 0;
+                cx[u] = ch ? __ldg(&a.rowptr[h.w[u] + 1]) : 0;
+            }
 #pragma unroll
             for (int u = 0; u < kSlotBatch; ++u) {
                 if (h.w[u] >= 0) {
-                    a.order[at] = h.w[u];
-                    a.level[h.w[u]] = nlev;
-                    a.parent[h.w[u]] = h.v;
-                    a.pedge[h.w[u]] = ce[u];
+                    bfs_put(a, nlev, h.v, h.w[u], ce[u], cb[u], cx[u], at);
                     ++at;
                 }
             }

@@ -181,9 +181,10 @@ template <class T> __global__ void k_face_final(int64_t n, T *g0, const T *__res
 // ------------------------------------------------------------------ face ADMM
 
 // Static per-face data of the face form (FP64 arithmetic, stored as T):
-// rec[16 f + 4 k + c] the unit vector of the edge opposite corner k (c < 3)
-// and rec[16 f + 4 k + 3] the twin weight A'/(A + A') (0 on a boundary
-// slot); rec[16 f + 12] = alpha = sqrt(A_f).
+// rec[12 f + 4 k + c] the unit vector of the edge opposite corner k (c < 3)
+// and rec[12 f + 4 k + 3] the twin weight A'/(A + A') (0 on a boundary
+// slot), 48 bytes per face in FP32; after all faces, rec[12 nf + f] =
+// alpha = sqrt(A_f), read only for the residuals.
 template <class T>
 __global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32_t *__restrict__ edges,
                            const int32_t *__restrict__ face_edge, const int32_t *__restrict__ twin,
@@ -191,7 +192,7 @@ __global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const double A = Af[f];
-    T *o = rec + 16 * f;
+    T *o = rec + 12 * f;
     for (int k = 0; k < 3; ++k) {
         double v[3];
         if (evf) {   // an intrinsic triangulation: the slot's vector in the face's own frame
@@ -209,8 +210,7 @@ __global__ void k_face_rec(int64_t nf, const double *__restrict__ P, const int32
         o[4 * k + 2] = (T)(v[2] * il);
         o[4 * k + 3] = (T)((tw >= 0) ? A2 / (A + A2) : 0.0);
     }
-    o[12] = (T)sqrt(A);
-    o[13] = o[14] = o[15] = T(0);
+    rec[12 * nf + f] = (T)sqrt(A);
 }
 
 // One ADMM iteration per face, Y then G then lambda (Sec. 3.2), with the
@@ -250,9 +250,10 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
                 if (s.in[k]) {
                     qn = T(2) * s.gn[c] - s.g[c] + s.q[k][c] - s.y[k][c];
                     if (part) {   // residual norms only when asked for (FP64 arithmetic is slow here)
-                        const T r = s.alpha * (s.y[k][c] - s.gn[c]);
+                        const T alpha = rec[12 * nf + f];
+                        const T r = alpha * (s.y[k][c] - s.gn[c]);
                         rp += (double)r * (double)r;
-                        const double dgv = (double)mu * (double)s.alpha * ((double)s.gn[c] - (double)s.g[c]);
+                        const double dgv = (double)mu * (double)alpha * ((double)s.gn[c] - (double)s.g[c]);
                         rd += dgv * dgv;
                     }
                 }
@@ -598,7 +599,7 @@ template <class T> gh_status face_rec(Ctx *c, DevMesh &m, const T *&out) {
     DBuf &buf = sizeof(T) == 4 ? m.face_rec32 : m.face_rec64;
     std::lock_guard<std::mutex> lk(*m.rec_mu);
     if (!buf.p) {
-        gh_status s = dalloc(c, buf, sizeof(T) * 16 * (size_t)m.nf);
+        gh_status s = dalloc(c, buf, sizeof(T) * 13 * (size_t)m.nf);
         if (s != GH_OK) return s;
         k_face_rec<T><<<blocks_for(m.nf, NT), NT, 0, c->stream>>>(m.nf, ptr<double>(m.P), ptr<int32_t>(m.edges),
                                                                  ptr<int32_t>(m.face_edge), ptr<int32_t>(m.twin),
