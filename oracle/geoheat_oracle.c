@@ -377,7 +377,7 @@ double orc_heat_residual(int64_t nv, const int32_t *rowptr, const int32_t *col, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Face-wise gradient normalisation (Alg. 1 line 2; eq.                      */
+/* Face-wise gradient normalisation (Algorithm 1; eq.                        */
 /* HeatDiffusionNormalization)                                               */
 /* ------------------------------------------------------------------------ */
 

@@ -1,4 +1,4 @@
-// Stages after the diffusion: face-wise gradient normalisation (Alg. 1 line 2,
+// Stages after the diffusion: face-wise gradient normalisation (Algorithm 1,
 // eq. HeatDiffusionNormalization), the face-based ADMM (Sec. 3.2), the
 // edge-based ADMM (Sec. 4.1), breadth-first integration (eq. IntegrationStep,
 // Sec. 4) and the heat residual E1 (eq. HeatSolutionError).
