@@ -36,6 +36,8 @@ struct BfsArgs {
     int32_t *lvl_off;
     int32_t *meta;
     int32_t n0;
+    const int32_t *targets;  // optional: stop once all of these have a set (their paths are then complete)
+    int32_t ntargets;
 };
 
 __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
@@ -350,6 +352,11 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         if (crank == 0 && threadIdx.x == 0) a.lvl_off[nlev] = hi;
         ++nlev;
         hi += total;
+        if (a.ntargets > 0) {   // every thread reads the same values after the barrier: a uniform decision
+            bool all = true;
+            for (int i = 0; i < a.ntargets; ++i) all = all && __ldcg(&a.level[a.targets[i]]) >= 0;
+            if (all) break;
+        }
     }
     if (crank == 0 && threadIdx.x == 0) {
         a.lvl_off[nlev] = hi;
@@ -559,7 +566,9 @@ bool bfs_cluster_supported(int cl) {
 // One breadth-first launch for all queries (query q on mesh *mq[q]), with
 // clusters of `cl` CTAs.
 static gh_status run_bfs_once(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
-                              const std::vector<std::vector<int32_t>> &src, int cl) {
+                              const std::vector<std::vector<int32_t>> &src, int cl,
+                              const std::vector<const int32_t *> *targets = nullptr,
+                              const std::vector<int32_t> *ntargets = nullptr) {
     cudaStream_t st = c->stream;
     int K = (int)src.size();
     std::vector<BfsArgs> args(K);
@@ -577,7 +586,7 @@ static gh_status run_bfs_once(Ctx *c, std::vector<DevMesh *> &mq, std::vector<Qu
                           ptr<int32_t>(w.parent), ptr<int32_t>(w.pedge), ptr<int32_t>(w.order),
                           ptr<int32_t>(w.pos), ptr<int32_t>(w.n0),
                           ptr<unsigned long long>(w.key), ptr<int32_t>(w.lvl_off), ptr<int32_t>(w.meta),
-                          (int32_t)src[q].size()};
+                          (int32_t)src[q].size(), targets ? (*targets)[q] : nullptr, ntargets ? (*ntargets)[q] : 0};
     }
     BfsArgs *dargs = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&dargs, sizeof(BfsArgs) * K, st));
@@ -599,8 +608,9 @@ static gh_status run_bfs_once(Ctx *c, std::vector<DevMesh *> &mq, std::vector<Qu
 }
 
 gh_status run_bfs_fixed(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws,
-                        const std::vector<std::vector<int32_t>> &src, int cl) {
-    return run_bfs_once(c, mq, ws, src, cl);
+                        const std::vector<std::vector<int32_t>> &src, int cl,
+                        const std::vector<const int32_t *> *targets, const std::vector<int32_t> *ntargets) {
+    return run_bfs_once(c, mq, ws, src, cl, targets, ntargets);
 }
 
 // The breadth-first sets of every query.  The cluster size is tuned per mesh,

@@ -267,9 +267,13 @@ gh_status mesh_intrinsic_delaunay(Ctx *c, DevMesh &m, int64_t *flips);
 gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
                   const std::vector<std::vector<int32_t>> &src);
 // the same with a given cluster size (8 is always supported), no tuning; any
-// graph in CSR form works (rowptr, col ascending, col_edge, nv of `meshes`)
+// graph in CSR form works (rowptr, col ascending, col_edge, nv of `meshes`).
+// targets (device, per query; may be null): the traversal may stop once all
+// of them have a set, leaving the later sets undone
 gh_status run_bfs_fixed(Ctx *c, std::vector<DevMesh *> &meshes, std::vector<QueryWs *> &ws,
-                        const std::vector<std::vector<int32_t>> &src, int cl);
+                        const std::vector<std::vector<int32_t>> &src, int cl,
+                        const std::vector<const int32_t *> *targets = nullptr,
+                        const std::vector<int32_t> *ntargets = nullptr);
 bool bfs_cluster_supported(int cl);
 gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t);
 

@@ -229,17 +229,34 @@ gh_status build_path_constraints(Ctx *c, std::vector<Item> &items) {
     }
     if (need.empty()) return GH_OK;
     // the traversal from each path query's first source (into the query's
-    // own traversal buffers, which its main traversal overwrites afterwards)
-    if (!mq.empty() && (s = run_bfs_fixed(c, mq, wq, sq, 8)) != GH_OK) return s;
+    // own traversal buffers, which its main traversal overwrites afterwards),
+    // stopped once it has reached the query's other sources
+    std::vector<const int32_t *> tg;
+    std::vector<int32_t> ntg;
+    for (size_t k : need) {
+        if (!npath[k]) continue;
+        QueryWs &w = *items[k].w;
+        const std::vector<int32_t> &src = *items[k].src;
+        if ((s = dalloc(c, w.pc_src, sizeof(int32_t) * src.size())) != GH_OK) return s;
+        GH_CUDA(cudaMemcpyAsync(w.pc_src.p, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, st));
+        tg.push_back(ptr<int32_t>(w.pc_src) + 1);
+        ntg.push_back((int32_t)src.size() - 1);
+    }
+    int cl = 8;   // the single-query cluster size of the meshes, when tuned and shared
+    if (!mq.empty()) {
+        std::lock_guard<std::mutex> lk(*mq[0]->rec_mu);
+        if (mq[0]->bfs_cluster[0] != 0) cl = mq[0]->bfs_cluster[0];
+    }
+    for (DevMesh *x : mq)
+        if (x != mq[0]) cl = 8;
+    if (!mq.empty() && (s = run_bfs_fixed(c, mq, wq, sq, cl, &tg, &ntg)) != GH_OK) return s;
     std::vector<std::vector<int32_t>> lv(items.size());
     for (size_t k : need) {
         if (!npath[k]) continue;
         QueryWs &w = *items[k].w;
         const std::vector<int32_t> &src = *items[k].src;
         const int ns = (int)src.size();
-        if ((s = dalloc(c, w.pc_src, sizeof(int32_t) * ns)) != GH_OK) return s;
         if ((s = dalloc(c, w.pc_lv, sizeof(int32_t) * ns)) != GH_OK) return s;
-        GH_CUDA(cudaMemcpyAsync(w.pc_src.p, src.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st));
         k_pc_levels<<<1, 32, 0, st>>>(ptr<int32_t>(w.pc_src), ns, ptr<int32_t>(w.level), ptr<int32_t>(w.pc_lv));
         ++c->launches;
         lv[k].resize(ns);
