@@ -107,7 +107,7 @@ bool is_device_ptr(const void *p) {
 }
 
 void free_ws(Ctx *c, QueryWs *w) {
-    DBuf *all[] = {&w->level, &w->parent, &w->pedge, &w->order, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->twid, &w->gent,
+    DBuf *all[] = {&w->level, &w->parent, &w->pedge, &w->order, &w->lorder, &w->pos, &w->key, &w->lvl_off, &w->meta, &w->twid, &w->gent,
                    &w->diag, &w->tiles, &w->ptile, &w->U0, &w->U1, &w->h, &w->g0, &w->g1, &w->l0, &w->l1, &w->z,
                    &w->w, &w->lam, &w->sz, &w->x, &w->inc, &w->d0, &w->d1, &w->n0, &w->n1, &w->resid, &w->e1, &w->actl,
                    &w->pc_src, &w->pc_lv, &w->pc_off, &w->pc_var, &w->pc_coef, &w->pc_entu, &w->pc_uvar,
@@ -131,7 +131,7 @@ static gh_status ensure_ws(Ctx *c, const DevMesh &m, QueryWs &w, int fp64, int f
     }
     gh_status s;
 #define A(buf, bytes) if ((s = dalloc(c, w.buf, (size_t)(bytes))) != GH_OK) return s
-    A(level, 4 * nv); A(parent, 4 * nv); A(pedge, 4 * nv); A(order, 4 * nv); A(pos, 4 * nv); A(key, 8 * nv);
+    A(level, 4 * nv); A(parent, 4 * nv); A(pedge, 4 * nv); A(order, 4 * nv); A(lorder, 4 * nv); A(pos, 4 * nv); A(key, 8 * nv);
     A(lvl_off, 4 * (nv + 2)); A(meta, 16);
     // padded so 16-byte aligned bulk copies of any row window stay inside the buffers
     A(gent, (nnz + 4) * (fp64 ? 16 : 8)); A(diag, es * (nv + 4));   // gent grows to the padded blocks
@@ -176,7 +176,7 @@ gh_status validate_params(const gh_params *p) {
 size_t ws_bytes(const DevMesh &m, int fp64, int form, int path_constraints) {
     const size_t es = fp64 ? 8 : 4, xs = fp64 ? 16 : 8;
     size_t nv = m.nv, nf = m.nf, ne = m.ne;
-    size_t b = nv * (5 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) + es * 3 * nf;
+    size_t b = nv * (6 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) + es * 3 * nf;
     b += (form == GH_FORM_FACE) ? es * 24 * nf : es * (9 * nf + 2 * ne);
     // path constraints: the block's variable map and an allowance for the entries
     // (sources x sets; their allocations are checked against the budget anyway)
@@ -666,7 +666,7 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out) {
     case GH_DUMP_LEVEL_OFF: return cp(w->lvl_off, 4 * n);
     case GH_DUMP_U_MANT:
     case GH_DUMP_U_EXP: {
-        // state is in queue order; scatter back to vertex order
+        // state is in layout order; scatter back to vertex order
         std::vector<int32_t> pos(m.nv);
         GH_CUDA(cudaMemcpy(pos.data(), w->pos.p, 4 * m.nv, cudaMemcpyDeviceToHost));
         const DBuf &U = w->final_buf ? w->U1 : w->U0;

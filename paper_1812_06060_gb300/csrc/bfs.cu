@@ -387,6 +387,68 @@ __global__ void k_row_len(const int32_t *__restrict__ order, int n, const int32_
     }
 }
 
+// Layout order.  The rows of one set are updated together from the previous
+// sweep's values of their own set (eq. HeatDiffusionUpdate), so their positions
+// may be permuted freely: each row keeps its entries in their order and every
+// iterate stays the same.  The layout stable-partitions each set into the rows
+// of at most `split` entries, then the longer ones, so a tile of short rows is
+// not padded to the longest row of its set (on a grid whose vertices
+// alternate between 4 and 8 neighbours, half the tiles drop from width 8 to 4).
+constexpr int kLenBins = 32;   // row lengths >= kLenBins - 1 share the last bin
+
+__global__ void k_len_hist(const int32_t *__restrict__ len, int n, int32_t *hist) {
+    __shared__ int32_t h[kLenBins];
+    if (threadIdx.x < kLenBins) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        atomicAdd(&h[min(len[r], kLenBins - 1)], 1);
+    __syncthreads();
+    if (threadIdx.x < kLenBins && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// the split that minimises the padded entries when the short part is padded
+// to `split` and the long part to the longest row (one thread; kLenBins bins)
+__global__ void k_pick_split(const int32_t *__restrict__ hist, int32_t *split) {
+    if (threadIdx.x != 0) return;
+    int lmax = 0;
+    int64_t n = 0;
+    for (int b = 0; b < kLenBins; ++b) {
+        n += hist[b];
+        if (hist[b]) lmax = b;
+    }
+    int best = lmax;
+    int64_t best_cost = n * lmax, below = 0;
+    for (int b = 0; b < lmax; ++b) {
+        below += hist[b];
+        if (!hist[b]) continue;
+        const int64_t cost = below * b + (n - below) * lmax;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = b;
+        }
+    }
+    *split = best;
+}
+
+__global__ void k_split_flag(const int32_t *__restrict__ len, int n, const int32_t *__restrict__ split, int32_t *flag) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) flag[r] = len[r] > *split ? 1 : 0;
+}
+
+// lorder: the set's short rows in queue order, then its long rows in queue
+// order; nlong_before is the exclusive scan of the long-row flags (n + 1 values)
+__global__ void k_split_scatter(const int32_t *__restrict__ order, int n, const int32_t *__restrict__ level,
+                                const int32_t *__restrict__ lvl_off, const int32_t *__restrict__ flag,
+                                const int32_t *__restrict__ nlong_before, int32_t *lorder) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int v = order[r], s = level[v];
+    const int b = lvl_off[s], e = lvl_off[s + 1];
+    const int before = nlong_before[r] - nlong_before[b];
+    const int nlong = nlong_before[e] - nlong_before[b];
+    lorder[flag[r] ? e - nlong + before : r - before] = v;
+}
+
 // Level-ordered operator, one block per tile in column-major ("ELL") order:
 // entry a of the row at tile position p (queue position start + p) sits at
 // gent[eb + a * cp + p], cp = count rounded up to 32, for a < W (the tile's
@@ -671,14 +733,30 @@ gh_status run_bfs(Ctx *c, std::vector<DevMesh *> &mq, std::vector<QueryWs *> &ws
 gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
     cudaStream_t st = c->stream;
     int n = q.nreach;
-    GH_CUDA(cudaMemsetAsync(q.pos.p, 0xff, sizeof(int32_t) * m.nv, st));
-    k_pos<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(q.pos)); ++c->launches;
+    const size_t tiles_cap = (size_t)n / TILE + (size_t)q.nlev + 2;
+    gh_status s;
+    if ((s = dalloc(c, q.tiles, sizeof(TileDesc) * tiles_cap)) != GH_OK) return s;
+    if ((s = dalloc(c, q.twid, sizeof(int32_t) * std::max<size_t>(2 * tiles_cap + 2, kLenBins + 1))) != GH_OK) return s;
     int32_t *len = ptr<int32_t>(q.n0);
     k_row_len<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), len); ++c->launches;
-    const size_t tiles_cap = (size_t)n / TILE + (size_t)q.nlev + 2;
-    gh_status s = dalloc(c, q.tiles, sizeof(TileDesc) * tiles_cap);
-    if (s != GH_OK) return s;
-    if ((s = dalloc(c, q.twid, sizeof(int32_t) * (2 * tiles_cap + 2))) != GH_OK) return s;
+    {
+        // the layout order: each set's short rows, then its long ones (histogram
+        // and split in twid, the flags' scan (n + 1 values) in the traversal's
+        // key buffer, free now)
+        int32_t *hist = ptr<int32_t>(q.twid), *split = hist + kLenBins, *flag = ptr<int32_t>(q.n1);
+        int32_t *nlong = reinterpret_cast<int32_t *>(ptr<unsigned long long>(q.key));
+        GH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * kLenBins, st));
+        k_len_hist<<<std::min(blocks_for(n, 256), 4u * 152u), 256, 0, st>>>(len, n, hist); ++c->launches;
+        k_pick_split<<<1, 32, 0, st>>>(hist, split); ++c->launches;
+        k_split_flag<<<blocks_for(n, 256), 256, 0, st>>>(len, n, split, flag); ++c->launches;
+        if ((s = exclusive_scan_u32_dev(c, flag, nlong, n)) != GH_OK) return s;
+        k_split_scatter<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.order), n, ptr<int32_t>(q.level),
+                                                           ptr<int32_t>(q.lvl_off), flag, nlong,
+                                                           ptr<int32_t>(q.lorder)); ++c->launches;
+    }
+    GH_CUDA(cudaMemsetAsync(q.pos.p, 0xff, sizeof(int32_t) * m.nv, st));
+    k_pos<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.lorder), n, ptr<int32_t>(q.pos)); ++c->launches;
+    k_row_len<<<blocks_for(n, 256), 256, 0, st>>>(ptr<int32_t>(q.lorder), n, ptr<int32_t>(m.rowptr), len); ++c->launches;
     k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.ptile), ptr<TileDesc>(q.tiles)); ++c->launches;
     const int n_even = (q.nlev + 1) / 2, n_odd = q.nlev / 2;
     int32_t *wsize = ptr<int32_t>(q.twid), *eoff = wsize + tiles_cap + 1;
@@ -692,12 +770,12 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
     if ((s = dalloc(c, q.gent, es * ((size_t)total + 4))) != GH_OK) return s;
     if (q.fp64) {
         k_fill_ell<double><<<(unsigned)tiles_cap, TILE, 0, st>>>(
-            ptr<int32_t>(q.ptile), n_even, n_odd, ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
+            ptr<int32_t>(q.ptile), n_even, n_odd, ptr<int32_t>(q.lorder), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
             ptr<int32_t>(m.col_edge), ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), eoff, t,
             ptr<TileDesc>(q.tiles), ptr<Ent<double>>(q.gent), ptr<double>(q.diag), c->status_dev); ++c->launches;
     } else {
         k_fill_ell<float><<<(unsigned)tiles_cap, TILE, 0, st>>>(
-            ptr<int32_t>(q.ptile), n_even, n_odd, ptr<int32_t>(q.order), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
+            ptr<int32_t>(q.ptile), n_even, n_odd, ptr<int32_t>(q.lorder), n, ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
             ptr<int32_t>(m.col_edge), ptr<double>(m.theta), ptr<double>(m.Av), ptr<int32_t>(q.pos), eoff, t,
             ptr<TileDesc>(q.tiles), ptr<Ent<float>>(q.gent), ptr<float>(q.diag), c->status_dev); ++c->launches;
     }

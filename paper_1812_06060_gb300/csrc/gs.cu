@@ -30,8 +30,9 @@
 // CTA, so the lowest unfinished tile can always run and the kernel cannot
 // deadlock (all CTAs are resident: cooperative launch).
 //
-// Vertices sit in breadth-first queue order, so D_i is a contiguous range and
-// the set of a neighbour follows from its position alone.  A tile is TILE
+// Vertices sit in breadth-first set order (inside a set, the rows with few
+// entries first), so D_i is a contiguous range and the set of a neighbour
+// follows from its position alone.  A tile is TILE
 // consecutive positions inside one set; its rows are one column-major block
 // (entry a of position p at a * cp + p, padded with zero-weight entries to the
 // tile's longest row), so the 32 lanes of a warp reading entry a of their
@@ -281,6 +282,57 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// The rows of one tile (consumer warp cw's positions), the first D entries of
+// each row held in registers; entries past D (tiles wider than kMaxDeg only)
+// are read one at a time.  Ucur / Uprv: this and the previous sweep's state.
+template <class T, int D>
+__device__ __forceinline__ void gs_tile_rows(XVal<T> *Ucur, const XVal<T> *Uprv, const Ent<T> *E, const T *sdiag,
+                                             int zero_pos, int start, int count, int lo, int cp, int wt, int sd,
+                                             int cw, int lane) {
+    XVal<T> u[kVPT][D];
+#pragma unroll
+    for (int v = 0; v < kVPT; ++v) {
+        const int p = v * 32 * kCW + cw * 32 + lane;
+        // all gathers of the thread go out together; entries past the
+        // block's width read the zero state kept at position nreach
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int c = zero_pos;
+            if (p < count && a < wt) c = E[a * cp + p].col;
+            u[v][a] = ld_state((c < lo ? Ucur : Uprv) + c);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kVPT; ++v) {
+        const int p = v * 32 * kCW + cw * 32 + lane;
+        if (p >= count) continue;
+        const int r = start + p;
+        // the sum is formed relative to its largest exponent (u_0 = 1 = 0.5 * 2^1 on the sources)
+        int eref = (lo == 0) ? 1 : kZeroExp;   // zero states carry kZeroExp: no test needed
+#pragma unroll
+        for (int a = 0; a < D; ++a) eref = max(eref, u[v][a].e);
+        for (int a = D; a < wt; ++a) {  // rows longer than D (tiles wider than kMaxDeg)
+            const Ent<T> x = E[a * cp + p];
+            const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
+            if (w.m != T(0)) eref = max(eref, w.e);
+        }
+        T acc = (lo == 0) ? xscale(T(0.5), 1 - eref) : T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const T w = (a < wt) ? E[a * cp + p].w : T(0);
+            acc += w * xscale(u[v][a].m, u[v][a].e - eref);
+        }
+        for (int a = D; a < wt; ++a) {
+            const Ent<T> x = E[a * cp + p];
+            const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
+            acc += x.w * xscale(w.m, w.e - eref);
+        }
+        XVal<T> out;
+        xnorm(acc * sdiag[r - sd], eref, out.m, out.e);   // diag holds 1 / (A_v + t sum theta)
+        Ucur[r] = out;
+    }
+}
+
 // Producer warp (one lane): for each of this CTA's tiles, in order, wait until
 // the staging buffer is free, stage the tile's row data with bulk copies,
 // look up the next tile, wait for the tile's three predecessor sets, then
@@ -423,48 +475,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         XVal<T> *Ucur = J.U[k & 1];
         const XVal<T> *Uprv = J.U[(k & 1) ^ 1];
         const Ent<T> *E = fits ? S.ent : J.gent + S.e0;   // the tile's row block
-        XVal<T> u[kVPT][kMaxDeg];
-#pragma unroll
-        for (int v = 0; v < kVPT; ++v) {
-            const int p = v * 32 * kCW + cw * 32 + lane;
-            // all gathers of the thread go out together; entries past the
-            // block's width read the zero state kept at position nreach
-#pragma unroll
-            for (int a = 0; a < kMaxDeg; ++a) {
-                int c = J.zero_pos;
-                if (p < count && a < wt) c = E[a * cp + p].col;
-                u[v][a] = ld_state((c < lo ? Ucur : Uprv) + c);
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < kVPT; ++v) {
-            const int p = v * 32 * kCW + cw * 32 + lane;
-            if (p >= count) continue;
-            const int r = start + p;
-            // the sum is formed relative to its largest exponent (u_0 = 1 = 0.5 * 2^1 on the sources)
-            int eref = (lo == 0) ? 1 : kZeroExp;   // zero states carry kZeroExp: no test needed
-#pragma unroll
-            for (int a = 0; a < kMaxDeg; ++a) eref = max(eref, u[v][a].e);
-            for (int a = kMaxDeg; a < wt; ++a) {  // rows longer than kMaxDeg
-                const Ent<T> x = E[a * cp + p];
-                const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
-                if (w.m != T(0)) eref = max(eref, w.e);
-            }
-            T acc = (lo == 0) ? xscale(T(0.5), 1 - eref) : T(0);
-#pragma unroll
-            for (int a = 0; a < kMaxDeg; ++a) {
-                const T w = (a < wt) ? E[a * cp + p].w : T(0);
-                acc += w * xscale(u[v][a].m, u[v][a].e - eref);
-            }
-            for (int a = kMaxDeg; a < wt; ++a) {
-                const Ent<T> x = E[a * cp + p];
-                const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
-                acc += x.w * xscale(w.m, w.e - eref);
-            }
-            XVal<T> out;
-            xnorm(acc * S.diag[r - sd], eref, out.m, out.e);   // diag holds 1 / (A_v + t sum theta)
-            Ucur[r] = out;
-        }
+        // the tile's width picks how many entries of a row sit in registers,
+        // so a tile of short rows does no arithmetic on padding (the skipped
+        // terms are exact zeros: the result is the same)
+        if (wt <= 4)
+            gs_tile_rows<T, 4>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
+        else if (wt <= 6)
+            gs_tile_rows<T, 6>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
+        else
+            gs_tile_rows<T, kMaxDeg>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
         __syncwarp();
         if (lane == 0) {
             // the last warp of the tile publishes it with one release add

@@ -178,6 +178,7 @@ struct QueryWs {
     // breadth-first traversal
     DBuf level, parent, order, pos, key, lvl_off, meta;  // meta: [0] nlev [1] nreach [2] err
     DBuf pedge;     // int32 [nv] edge from each vertex to its pairing vertex
+    DBuf lorder;    // int32 [nv] layout order: the queue with each set's short rows first; pos is its inverse
     // level-ordered Gauss-Seidel layout
     DBuf gent;      // Ent<T>: one column-major block per tile (see k_fill_ell)
     DBuf twid;      // int32 [2 tiles + 2]: block size and offset of each tile

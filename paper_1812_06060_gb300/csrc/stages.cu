@@ -549,7 +549,7 @@ __global__ void k_jump(int64_t nv, const double *__restrict__ d_in, const int32_
 
 // ------------------------------------------------------------------ heat residual
 
-// per reached vertex r (queue order): (A - t L_c) u - u_0 in FP64
+// per reached vertex r (layout order): (A - t L_c) u - u_0 in FP64
 template <class T>
 __global__ void __launch_bounds__(NT) k_heat_resid(int n, const int32_t *__restrict__ order,
                                                    const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -731,7 +731,7 @@ template <class T> gh_status heat_resid_t(Ctx *c, const DevMesh &m, QueryWs &q) 
     unsigned nb = blocks_for(n, NT);
     double *part = nullptr;
     GH_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * nb, st));
-    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.order), ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
+    k_heat_resid<T><<<nb, NT, 0, st>>>(n, ptr<int32_t>(q.lorder), ptr<int32_t>(m.rowptr), ptr<int32_t>(m.col),
                                        ptr<int32_t>(m.col_edge), ptr<double>(m.theta), ptr<int32_t>(q.pos), q.t,
                                        ptr<T>(q.diag), ptr<int32_t>(q.lvl_off), ptr<XVal<T>>(q.final_buf ? q.U1 : q.U0),
                                        part); ++c->launches;
