@@ -221,6 +221,24 @@ def heat_residual(md: MeshData, b: BFS, t: float, state) -> float:
                                    t, _p(b.level), _p(um), _p(ue))
 
 
+def gs_until(md: MeshData, b: BFS, t: float, max_sweeps: int, tol: float, check: int):
+    """Gauss-Seidel diffusion stopped on the heat residual E1 (eq.
+    HeatSolutionError): E1 is evaluated after every ``check`` sweeps (and
+    after the last), and the sweeps end at the first evaluation with
+    E1 <= tol, or after max_sweeps.  Each round resumes the same iteration
+    (the state is the whole iterate).  Returns (state, sweeps run, the E1
+    of every evaluation)."""
+    st, done, hist = None, 0, []
+    while done < max_sweeps:
+        k = min(check, max_sweeps - done)
+        st = gs(md, b, t, k, st)
+        done += k
+        hist.append(heat_residual(md, b, t, st))
+        if hist[-1] <= tol:
+            break
+    return st, done, hist
+
+
 def normalize(md: MeshData, state) -> np.ndarray:
     """h = -grad u / |grad u| per face (eq. HeatDiffusionNormalization)."""
     um, ue = state
@@ -574,19 +592,24 @@ def diffusion_time(md: MeshData, m: float = 1.0) -> float:
 
 def solve(md: MeshData, sources, form: str = "edge", sweeps: int = 200, m: float = 1.0, t: float | None = None,
           admm_iters: int = ADMM_ITERS, mu: float = MU, eps=None, path_constraints_on: bool = False,
-          cycle_constraints_on: bool = False) -> dict:
+          cycle_constraints_on: bool = False, gs_tol: float = 0.0, gs_check: int = 100) -> dict:
     """Algorithm 1 end to end: Diffusion -> normalise -> Integrable ->
     Recovery, in the face form (Sec. 3) or the edge form (Sec. 4).  Returns
     every intermediate.  eps = (eps1, eps2) ends the ADMM early on its
     residuals (Sec. 3.2); the iterations run are len(out["res"]).
     path_constraints_on adds the multi-source constraints (Sec. 5.2),
     cycle_constraints_on the cycle constraints of a closed mesh of genus
-    g >= 1 (Sec. 5.1), after the path constraints."""
+    g >= 1 (Sec. 5.1), after the path constraints.  gs_tol > 0 stops the
+    diffusion on E1 (gs_until, at most ``sweeps``); out["gs_sweeps"] is the
+    number of sweeps run."""
     t = diffusion_time(md, m) if t is None else t
     b = bfs(md, sources)
-    st = gs(md, b, t, sweeps)
+    if gs_tol > 0:
+        st, nsw, _ = gs_until(md, b, t, sweeps, gs_tol, gs_check)
+    else:
+        st, nsw = gs(md, b, t, sweeps), sweeps
     h = normalize(md, st)
-    out = {"t": t, "bfs": b, "u": st, "h": h}
+    out = {"t": t, "bfs": b, "u": st, "h": h, "gs_sweeps": nsw}
     parts = []
     if path_constraints_on:
         parts.append(path_constraints(md, sources, form))
