@@ -98,6 +98,21 @@ typedef enum { GH_FORM_FACE = 0, GH_FORM_EDGE = 1 } gh_form;
  *              vertex 0 and face 0.  A mesh with boundary edges or in several
  *              pieces gets none.  Path and cycle constraints together: at
  *              most 31 (GH_EINVAL otherwise).  Default 0.
+ *  gs_tol      > 0: stop the diffusion on the heat residual E1 (eq.
+ *              HeatSolutionError, the l2 norm of (A - t L_c) u - u_0 over
+ *              the reached vertices, in FP64 from the state and the
+ *              weights the sweeps use): E1 is evaluated after every
+ *              gs_check sweeps and after the last, and the sweeps end at
+ *              the first evaluation with E1 <= gs_tol, at most gs_sweeps in
+ *              all.  The rounds continue one iteration: the state after n
+ *              sweeps is the same, bit for bit, as that of an uninterrupted
+ *              run of n sweeps.  Each round refills the pipelined sweeps
+ *              (a round of c sweeps costs about L + 2c set steps instead of
+ *              2c), so gs_check well above the number of breadth-first sets
+ *              keeps the overhead small.  The sweeps run are readable with
+ *              gh_debug_dump (GH_DUMP_GS_SWEEPS).  0 (the default): exactly
+ *              gs_sweeps sweeps.  Must be finite and >= 0.
+ *  gs_check    sweeps per E1 evaluation when gs_tol > 0; >= 1.  Default 100.
  */
 typedef struct {
     double m;
@@ -113,6 +128,8 @@ typedef struct {
     double eps2;
     int32_t path_constraints;
     int32_t cycle_constraints;
+    double gs_tol;
+    int32_t gs_check;
 } gh_params;
 
 /* Fills *p with the defaults listed above. */
@@ -288,7 +305,8 @@ typedef enum {
     GH_DUMP_PC_VAR = 23,    /* int32 [n]     constrained variable of each entry: edge id (edge form), face id (face form) */
     GH_DUMP_PC_COEF = 24,   /* float64 [n][dim] coefficient of each entry: sign (edge form), path edge vector (face form) */
     GH_DUMP_FACES = 25,     /* int32 [nf][3] the faces of the mesh's triangulation */
-    GH_DUMP_ELEN = 26       /* float64 [ne]  edge lengths */
+    GH_DUMP_ELEN = 26,      /* float64 [ne]  edge lengths */
+    GH_DUMP_GS_SWEEPS = 27  /* int32 [1]     Gauss-Seidel sweeps run (gs_tol can end them before gs_sweeps) */
 } gh_dump_item;
 
 gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *count, int32_t *elem_bytes);

@@ -27,7 +27,7 @@ GH_FORM_FACE, GH_FORM_EDGE = 0, 1
 (GH_DUMP_LEVEL, GH_DUMP_PARENT, GH_DUMP_ORDER, GH_DUMP_LEVEL_OFF, GH_DUMP_U_MANT, GH_DUMP_U_EXP, GH_DUMP_H,
  GH_DUMP_G, GH_DUMP_X, GH_DUMP_D, GH_DUMP_EDGES, GH_DUMP_FACE_EDGE, GH_DUMP_FACE_SIGN, GH_DUMP_THETA, GH_DUMP_AV,
  GH_DUMP_AF, GH_DUMP_ROWPTR, GH_DUMP_COL, GH_DUMP_RESID, GH_DUMP_E1, GH_DUMP_T, GH_DUMP_ITERS, GH_DUMP_PC_OFF,
- GH_DUMP_PC_VAR, GH_DUMP_PC_COEF, GH_DUMP_FACES, GH_DUMP_ELEN) = range(27)
+ GH_DUMP_PC_VAR, GH_DUMP_PC_COEF, GH_DUMP_FACES, GH_DUMP_ELEN, GH_DUMP_GS_SWEEPS) = range(28)
 
 STATUS_NAMES = {0: "GH_OK", 1: "GH_EINVAL", 2: "GH_ENOMEM", 3: "GH_EDEVICE", 4: "GH_ETIMEOUT", 5: "GH_EBUSY",
                 6: "GH_ENOTFOUND", 7: "GH_ENONMANIFOLD"}
@@ -44,7 +44,8 @@ class GhParams(C.Structure):
     _fields_ = [("m", C.c_double), ("t", C.c_double), ("gs_sweeps", C.c_int32), ("admm_iters", C.c_int32),
                 ("mu", C.c_double), ("form", C.c_int32), ("fp64", C.c_int32), ("diagnostics", C.c_int32),
                 ("early_stop", C.c_int32), ("eps1", C.c_double), ("eps2", C.c_double),
-                ("path_constraints", C.c_int32), ("cycle_constraints", C.c_int32)]
+                ("path_constraints", C.c_int32), ("cycle_constraints", C.c_int32), ("gs_tol", C.c_double),
+                ("gs_check", C.c_int32)]
 
 
 class GeoheatError(RuntimeError):
@@ -128,10 +129,12 @@ def _check(rc: int):
 
 
 def params(m=1.0, t=0.0, gs_sweeps=200, admm_iters=10, mu=100.0, form="edge", fp64=False, diagnostics=False,
-           eps=None, path_constraints=False, cycle_constraints=False):
+           eps=None, path_constraints=False, cycle_constraints=False, gs_tol=0.0, gs_check=100):
     """Solver parameters; eps = (eps1, eps2) turns on early termination of the
     ADMM; path_constraints adds the multi-source path constraints,
-    cycle_constraints the cycle constraints of a closed mesh of genus >= 1."""
+    cycle_constraints the cycle constraints of a closed mesh of genus >= 1;
+    gs_tol > 0 ends the diffusion once the heat residual E1 is within it
+    (checked every gs_check sweeps, at most gs_sweeps)."""
     p = GhParams()
     lib().gh_params_default(C.byref(p))
     p.m, p.t, p.gs_sweeps, p.admm_iters, p.mu = m, t, gs_sweeps, admm_iters, mu
@@ -141,6 +144,7 @@ def params(m=1.0, t=0.0, gs_sweeps=200, admm_iters=10, mu=100.0, form="edge", fp
         p.early_stop, p.eps1, p.eps2 = 1, float(eps[0]), float(eps[1])
     p.path_constraints = int(bool(path_constraints))
     p.cycle_constraints = int(bool(cycle_constraints))
+    p.gs_tol, p.gs_check = float(gs_tol), int(gs_check)
     return p
 
 

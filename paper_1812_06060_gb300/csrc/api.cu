@@ -169,6 +169,8 @@ gh_status validate_params(const gh_params *p) {
         set_error("cycle_constraints must be 0 or 1");
         return GH_EINVAL;
     }
+    if (!(p->gs_tol >= 0 && p->gs_tol < 1e300)) { set_error("gs_tol must be finite and >= 0"); return GH_EINVAL; }
+    if (p->gs_tol > 0 && p->gs_check < 1) { set_error("gs_check must be >= 1 when gs_tol > 0"); return GH_EINVAL; }
     return GH_OK;
 }
 
@@ -182,6 +184,58 @@ size_t ws_bytes(const DevMesh &m, int fp64, int form, int path_constraints) {
     // (sources x sets; their allocations are checked against the budget anyway)
     if (path_constraints) b += 4 * ((form == GH_FORM_FACE) ? nf : ne) + (size_t)(kMaxPc + 1) * 64 * 1024;
     return b + (1 << 20);
+}
+
+// The diffusion of every query: gs_sweeps sweeps in one launch for all; the
+// queries with gs_tol > 0 go in rounds of gs_check sweeps, each continuing
+// the iteration of the last, until their heat residual E1 (eq.
+// HeatSolutionError) is within gs_tol or gs_sweeps sweeps have run; every
+// round is one launch for the queries still running.  ev0 / ev1 bracket all
+// rounds.
+static gh_status run_diffusion(Ctx *c, std::vector<Item> &items, std::vector<QueryWs *> &ws, cudaEvent_t ev0,
+                               cudaEvent_t ev1) {
+    const int K = (int)ws.size();
+    std::vector<int> left(K);
+    std::vector<QueryWs *> run;
+    for (int q = 0; q < K; ++q) {
+        ws[q]->gs_continue = 0;
+        ws[q]->sweeps_run = 0;
+        left[q] = items[q].p->gs_sweeps;
+    }
+    std::vector<int> active(K);
+    for (int q = 0; q < K; ++q) active[q] = q;
+    std::vector<double> e1(K, 0.0);
+    bool first = true;
+    while (!active.empty()) {
+        run.clear();
+        for (int q : active) {
+            const gh_params *p = items[q].p;
+            ws[q]->sweeps = (p->gs_tol > 0) ? std::min(p->gs_check, left[q]) : left[q];
+            run.push_back(ws[q]);
+        }
+        gh_status s = run_gs(c, run, first ? ev0 : nullptr, nullptr);
+        if (s != GH_OK) return s;
+        first = false;
+        std::vector<int> next;
+        for (int q : active) {
+            left[q] -= ws[q]->sweeps;
+            ws[q]->sweeps_run += ws[q]->sweeps;
+            ws[q]->gs_continue = 1;
+            if (items[q].p->gs_tol > 0) {
+                if ((s = run_heat_residual(c, *items[q].m, *ws[q])) != GH_OK) return s;
+                GH_CUDA(cudaMemcpyAsync(&e1[q], ws[q]->e1.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                next.push_back(q);
+            }
+        }
+        if (next.empty()) break;
+        GH_CUDA(cudaStreamSynchronize(c->stream));
+        if ((s = check_status(c, "diffusion")) != GH_OK) return s;
+        active.clear();
+        for (int q : next)
+            if (left[q] > 0 && !(e1[q] <= items[q].p->gs_tol)) active.push_back(q);
+    }
+    if (ev1) cudaEventRecord(ev1, c->stream);
+    return GH_OK;
 }
 
 // The whole path for a list of queries, each with its own mesh, workspace,
@@ -221,7 +275,7 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
         }
         if (s != GH_OK) break;
         cudaEventRecord(ev[1], c->stream);
-        if ((s = run_gs(c, ws, ev[6], ev[7])) != GH_OK) break;
+        if ((s = run_diffusion(c, items, ws, ev[6], ev[7])) != GH_OK) break;
         cudaEventRecord(ev[2], c->stream);
         // no host synchronisation here: a diffusion timeout leaves every index
         // in range, and the status word is read once the solve is done
@@ -390,6 +444,8 @@ void gh_params_default(gh_params *p) {
     p->eps2 = 1e-5;
     p->path_constraints = 0;
     p->cycle_constraints = 0;
+    p->gs_tol = 0.0;
+    p->gs_check = 100;
 }
 
 const char *gh_version(void) { return "geoheat 0.1 (sm_103a)"; }
@@ -621,6 +677,7 @@ gh_status gh_debug_size(gh_mesh mesh, int32_t query, int32_t what, int64_t *coun
         n = 1; eb = 8; break;
     case GH_DUMP_T: n = 1; eb = 8; break;
     case GH_DUMP_ITERS: n = 1; eb = 4; break;
+    case GH_DUMP_GS_SWEEPS: n = 1; eb = 4; break;
     case GH_DUMP_PC_OFF: n = w->pc_n ? w->pc_n + 1 : 0; break;
     case GH_DUMP_PC_VAR: n = w->pc_ent; break;
     case GH_DUMP_PC_COEF: n = (int64_t)w->pc_ent * w->pc_dim; eb = 8; break;
@@ -708,6 +765,7 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out) {
     case GH_DUMP_ITERS:
         GH_CUDA(cudaMemcpy(out, (const char *)w->actl.p + offsetof(AdmmCtl, iters_done), 4, cudaMemcpyDeviceToHost));
         return GH_OK;
+    case GH_DUMP_GS_SWEEPS: std::memcpy(out, &w->sweeps_run, 4); return GH_OK;
     case GH_DUMP_PC_OFF: return n ? cp(w->pc_off, 4 * n) : GH_OK;
     case GH_DUMP_PC_VAR: return n ? cp(w->pc_var, 4 * n) : GH_OK;
     case GH_DUMP_PC_COEF: return n ? cp(w->pc_coef, 8 * n) : GH_OK;

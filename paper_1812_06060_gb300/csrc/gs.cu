@@ -532,6 +532,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cu
     if (per_sm < 1) { set_error("diffusion kernel does not fit on an SM"); return GH_EDEVICE; }
     const int grid = std::max(1, per_sm * c->num_sms / std::max(1, c->gs_share));
     std::vector<GsJob<T>> jobs(K);
+    std::vector<int> prev_buf(K);
     size_t soff_total = 0;
     for (int q = 0; q < K; ++q) soff_total += (size_t)ws[q]->nlev + 2 * (size_t)ws[q]->sweeps + 2;
     int32_t *scratch = nullptr;   // per query: step counts and their prefix
@@ -560,13 +561,23 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cu
         j.U[1] = ptr<XVal<T>>(w.U1);
         j.zero_pos = w.nreach;
         jobs[q] = j;
+        prev_buf[q] = w.final_buf;
         w.final_buf = (w.sweeps - 1) & 1;
     }
     GH_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(GsJob<T>) * K, cudaMemcpyHostToDevice, st));
     std::vector<int32_t> ntick(K);
     for (int q = 0; q < K; ++q) {
         QueryWs &w = *ws[q];
-        k_zero_state<T><<<blocks_for(w.nreach + 1, 256), 256, 0, st>>>(jobs[q].U[0], jobs[q].U[1], w.nreach + 1); ++c->launches;
+        if (w.gs_continue) {
+            // resume: both buffers hold the last state (the first sweep reads
+            // its own and the next set's previous values from buffer 1, and
+            // overwrites buffer 0 set by set before any later set reads it)
+            GH_CUDA(cudaMemcpyAsync(jobs[q].U[prev_buf[q] ^ 1], jobs[q].U[prev_buf[q]], sizeof(XVal<T>) * (w.nreach + 1),
+                                    cudaMemcpyDeviceToDevice, st));
+        } else {
+            k_zero_state<T><<<blocks_for(w.nreach + 1, 256), 256, 0, st>>>(jobs[q].U[0], jobs[q].U[1], w.nreach + 1);
+            ++c->launches;
+        }
         GH_CUDA(cudaMemsetAsync(jobs[q].done, 0, sizeof(int32_t) * (w.nlev + 1), st));
         int32_t *cnt = const_cast<int32_t *>(jobs[q].stepoff) - soff_total;
         k_step_counts<T><<<blocks_for(jobs[q].nsteps, 256), 256, 0, st>>>(djobs, q, cnt); ++c->launches;
