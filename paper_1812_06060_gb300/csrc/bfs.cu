@@ -450,13 +450,13 @@ __global__ void k_split_scatter(const int32_t *__restrict__ order, int n, const 
 }
 
 // Level-ordered operator, one block per tile in column-major ("ELL") order:
-// entry a of the row at tile position p (queue position start + p) sits at
+// entry a of the row at tile position p (layout position start + p) sits at
 // gent[eb + a * cp + p], cp = count rounded up to 32, for a < W (the tile's
 // longest row); the entries of a row are its neighbours in ascending order,
-// renumbered to queue positions, with weight t*theta, and (zero slot n, 0)
+// renumbered to layout positions, with weight t*theta, and (zero slot n, 0)
 // past the row's end and in the padding columns.  A warp reading entry a of
 // 32 consecutive rows touches 32 consecutive entries.  idiag = 1 / (A_v +
-// t * sum theta) (FP64, then rounded).  A neighbour without a queue position
+// t * sum theta) (FP64, then rounded).  A neighbour without a layout position
 // would mean inconsistent breadth-first sets: it is pointed at the zero slot
 // and the status word reports it.
 
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(TILE) k_fill_ell(const int32_t *__restrict__ p
     }
 }
 
-// tiles of at most TILE queue positions inside one set, listed set by set,
+// tiles of at most TILE layout positions inside one set, listed set by set,
 // even sets first, then odd sets; ptile holds, per parity, the running tile
 // count before each set of that parity
 __device__ __forceinline__ int ntiles_of(const int32_t *lvl_off, int nlev, int i) {

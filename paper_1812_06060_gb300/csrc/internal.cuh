@@ -79,7 +79,7 @@ struct AdmmCtl {
     double th[2];   // |r_primal| and |r_dual| thresholds
 };
 
-// One Gauss-Seidel tile: up to TILE consecutive queue positions of one set.
+// One Gauss-Seidel tile: up to TILE consecutive layout positions of one set.
 struct alignas(16) TileDesc {
     int level, start, count, lo;      // set index, first position, positions, first position of the set
     int eb, ee, nt_prev, nt_self;     // first entry of its row block, width W; tiles in sets i-1 and i
@@ -246,7 +246,7 @@ bool is_device_ptr(const void *p);
 
 // ---------------------------------------------------------------- kernels (host launchers)
 
-constexpr int TILE = 512;  // queue positions per Gauss-Seidel tile
+constexpr int TILE = 512;  // layout positions per Gauss-Seidel tile
 
 // scan.cu
 gh_status exclusive_scan_i32(Ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *total_host);
