@@ -315,6 +315,60 @@ def strip_grid(nx: int, ny: int) -> Mesh:
     return Mesh(V=V, F=F, name=f"strip{nx}x{ny}", meta={"nx": nx, "ny": ny})
 
 
+def mixed_density_strip(nx: int, ny: int, dense: int = 3) -> Mesh:
+    """Strip of ny rows (y = row index, z = 0): even rows hold nx vertices
+    at unit spacing, odd rows dense * (nx - 1) + 1 vertices at spacing
+    1 / dense; consecutive rows are zipped into triangles from left to right
+    (the next triangle takes the lower row's next vertex while it lies no
+    further right than the upper row's next).  Interior sparse-row vertices
+    have 10 neighbours with dense = 3, so with the first row as sources whole
+    breadth-first sets consist of long rows."""
+    xs_rows, base = [], 0
+    V = []
+    for r in range(ny):
+        xs = np.arange(nx, dtype=np.float64) if r % 2 == 0 else np.arange(dense * (nx - 1) + 1) / dense
+        xs_rows.append((xs, base))
+        V.append(np.stack([xs, np.full(xs.size, float(r)), np.zeros(xs.size)], axis=1))
+        base += xs.size
+    F = []
+    for r in range(ny - 1):
+        (xb, b0), (xt, t0) = xs_rows[r], xs_rows[r + 1]
+        i = j = 0
+        while i < xb.size - 1 or j < xt.size - 1:
+            if j == xt.size - 1 or (i < xb.size - 1 and xb[i + 1] <= xt[j + 1]):
+                F.append((b0 + i, b0 + i + 1, t0 + j))
+                i += 1
+            else:
+                F.append((b0 + i, t0 + j + 1, t0 + j))
+                j += 1
+    return Mesh(V=np.concatenate(V), F=np.asarray(F, dtype=np.int32), name=f"mixedstrip{nx}x{ny}",
+                meta={"nx": nx, "ny": ny, "dense": dense})
+
+
+def jittered_delaunay(N: int, seed: int, jitter: float = 0.45) -> Mesh:
+    """Delaunay triangulation (scipy.spatial) of an N x N lattice on the unit
+    square (spacing h = 1 / (N - 1)), z = 0, faces turned counter-clockwise.
+    Inner points move by independent uniform offsets in [-jitter h, jitter h)
+    in x and y; boundary points stay put.  Unlike the fixed diagonals of
+    ``jittered_grid`` the connectivity follows the points: vertex degrees
+    vary from 3 to 10 around a mean of 6 (with jitter 0.45 no angle is below
+    about 4 degrees)."""
+    from scipy.spatial import Delaunay
+    rng = rng_for(seed)
+    h = 1.0 / (N - 1)
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    P = np.stack([(j * h).ravel(), (i * h).ravel()], axis=1)
+    inner = ((i > 0) & (i < N - 1) & (j > 0) & (j < N - 1)).ravel()
+    P[inner] += (rng.random((int(inner.sum()), 2)) * 2.0 - 1.0) * (jitter * h)
+    F = Delaunay(P).simplices.astype(np.int32)
+    a, b, c = P[F[:, 0]], P[F[:, 1]], P[F[:, 2]]
+    cw = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]) < 0
+    F[cw] = F[cw][:, [0, 2, 1]]
+    V = np.zeros((N * N, 3))
+    V[:, :2] = P
+    return Mesh(V=V, F=np.ascontiguousarray(F), name=f"delaunay{N}", meta={"N": N, "seed": seed, "jitter": jitter})
+
+
 # --------------------------------------------------------------------------
 # Source sets
 # --------------------------------------------------------------------------

@@ -84,3 +84,26 @@ def test_torus_is_closed_oriented_genus_one():
     core[:, 2] = 0
     core *= (1.0 / np.linalg.norm(core, axis=1))[:, None]
     assert np.all(np.einsum("ij,ij->i", n, p - core) > 0)
+
+
+def test_jittered_delaunay_is_an_oriented_disk_with_varied_degrees():
+    m = meshgen.jittered_delaunay(60, 5)
+    md = oracle.mesh_data(m.V, m.F)          # rejects inconsistent orientation
+    assert md.nv - md.ne + md.nf == 1        # a disk
+    P = m.V[m.F]
+    area = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])[:, 2]
+    assert np.all(area > 0) and 0.5 * area.sum() == pytest.approx(1.0, rel=1e-12)   # tiles the square
+    deg = np.diff(md.rowptr)
+    assert deg.min() <= 3 and deg.max() >= 9
+    assert np.array_equal(m.F, meshgen.jittered_delaunay(60, 5).F)   # seeded
+
+
+def test_mixed_density_strip_rows():
+    m = meshgen.mixed_density_strip(40, 5)
+    md = oracle.mesh_data(m.V, m.F)          # rejects inconsistent orientation
+    assert md.nv == 40 * 3 + 118 * 2 and md.nv - md.ne + md.nf == 1
+    P = m.V[m.F]
+    area = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])[:, 2]
+    assert np.all(area > 0) and 0.5 * area.sum() == pytest.approx(39.0 * 4, rel=1e-12)
+    deg = np.diff(md.rowptr)
+    assert np.all(deg[40 + 118 + 1:2 * 40 + 118 - 1] == 10)   # the interior of the middle sparse row
