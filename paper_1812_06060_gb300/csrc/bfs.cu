@@ -137,21 +137,31 @@ __device__ __forceinline__ void bfs_offer(const BfsArgs &a, int r, int b, int fr
     }
 }
 
+// A child placed at queue position at is, unless the next set is split
+// evenly, a parent of the placing CTA in the next set, at rank at - nbase of
+// the CTA's range; the first BT of them are also kept in shared memory, so
+// the next set's held rows need no round trip to L2.
+struct NextRow {
+    int v, b, e;
+};
+
 // writes one child w (pairing vertex p, pairing edge ce) at queue position
 // at, with its row bounds (loaded here, in the round trip of the edge id)
-__device__ __forceinline__ void bfs_put(const BfsArgs &a, int nlev, int p, int w, int ce, int rb, int re, int at) {
+__device__ __forceinline__ void bfs_put(const BfsArgs &a, int nlev, int p, int w, int ce, int rb, int re, int at,
+                                        NextRow *sn, int nbase) {
     a.order[at] = w;
     a.rb[at] = rb;
     a.re[at] = re;
     a.level[w] = nlev;
     a.parent[w] = p;
     a.pedge[w] = ce;
+    if ((unsigned)(at - nbase) < (unsigned)BT) sn[at - nbase] = NextRow{w, rb, re};
 }
 
 // writes the children of parent p (rank r, row [b, e)) among slots [from, e)
 // from queue position at on; returns the next position
 __device__ __forceinline__ int bfs_place(const BfsArgs &a, int nlev, int p, int r, int b, int from, int e,
-                                         unsigned mk, int at) {
+                                         unsigned mk, int at, NextRow *sn, int nbase) {
     for (int j0 = from; j0 < e; j0 += kSlotBatch) {
         int w[kSlotBatch];
         bool ch[kSlotBatch];
@@ -172,7 +182,7 @@ __device__ __forceinline__ int bfs_place(const BfsArgs &a, int nlev, int p, int 
 #pragma unroll
         for (int u = 0; u < kSlotBatch; ++u) {
             if (ch[u]) {
-                bfs_put(a, nlev, p, w[u], ce[u], cb[u], cx[u], at);
+                bfs_put(a, nlev, p, w[u], ce[u], cb[u], cx[u], at, sn, nbase);
                 ++at;
             }
         }
@@ -189,12 +199,19 @@ struct Held {
     int w[kSlotBatch];
 };
 
-// offers of rank r (its row bounds recorded at placement); the first slots
-// are kept in h
-__device__ __forceinline__ void bfs_offer_held(const BfsArgs &a, int r, Held &h) {
-    h.v = __ldcg(&a.order[r]);
-    h.b = __ldcg(&a.rb[r]);
-    h.e = __ldcg(&a.re[r]);
+// offers of rank r (its row bounds recorded at placement, or its entry of
+// the placing CTA's shared copy sn when own); the first slots are kept in h
+__device__ __forceinline__ void bfs_offer_held(const BfsArgs &a, int r, Held &h, const NextRow *sn, bool own) {
+    if (own) {
+        const NextRow x = sn[threadIdx.x];
+        h.v = x.v;
+        h.b = x.b;
+        h.e = x.e;
+    } else {
+        h.v = __ldcg(&a.order[r]);
+        h.b = __ldcg(&a.rb[r]);
+        h.e = __ldcg(&a.re[r]);
+    }
 #pragma unroll
     for (int u = 0; u < kSlotBatch; ++u) h.w[u] = h.b + u < h.e ? __ldg(&a.col[h.b + u]) : -1;
 #pragma unroll
@@ -203,13 +220,15 @@ __device__ __forceinline__ void bfs_offer_held(const BfsArgs &a, int r, Held &h)
     if (h.e > h.b + kSlotBatch) bfs_offer(a, r, h.b, h.b + kSlotBatch, h.e);
 }
 
-// the offers of the parents [plo, phi) of the next set
-__device__ __forceinline__ void bfs_offer_set(const BfsArgs &a, int plo, int phi, Held &h) {
+// the offers of the parents [plo, phi) of the next set (own: the CTA placed
+// them, and sn holds its shared copy of their first BT rows)
+__device__ __forceinline__ void bfs_offer_set(const BfsArgs &a, int plo, int phi, Held &h, const NextRow *sn,
+                                              bool own) {
     h.v = -1;
     h.b = h.e = 0;
 #pragma unroll
     for (int u = 0; u < kSlotBatch; ++u) h.w[u] = -1;
-    if (plo + (int)threadIdx.x < phi) bfs_offer_held(a, plo + (int)threadIdx.x, h);
+    if (plo + (int)threadIdx.x < phi) bfs_offer_held(a, plo + (int)threadIdx.x, h, sn, own);
     for (int r = plo + (int)threadIdx.x + BT; r < phi; r += BT) {
         const int b = __ldcg(&a.rb[r]), e = __ldcg(&a.re[r]);
         bfs_offer(a, r, b, b, e);
@@ -223,6 +242,7 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
     // the arguments stay in shared memory: registers go to the held rows
     __shared__ BfsArgs s_args;
     __shared__ int s_total;
+    __shared__ NextRow s_next[BT];
     if (threadIdx.x == 0) s_args = all[blockIdx.x / CL];
     __syncthreads();
     const BfsArgs &a = s_args;
@@ -241,7 +261,7 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
             a.re[r] = a.rowptr[v + 1];
         }
         __syncthreads();
-        bfs_offer_set(a, plo, phi, h);
+        bfs_offer_set(a, plo, phi, h, s_next, false);
     }
     cluster.sync();
     while (true) {
@@ -300,6 +320,7 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
         }
         // place the children: queue position hi + before + (children of this
         // CTA's earlier chunks) + (earlier parents of the chunk)
+        const int nbase = hi + before;
         if (k0) {
             int at = hi + before + ex0;
             int ce[kSlotBatch], cb[kSlotBatch], cx[kSlotBatch];   // all loads first: one round trip
@@ -313,12 +334,12 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
 #pragma unroll
             for (int u = 0; u < kSlotBatch; ++u) {
                 if (h.w[u] >= 0) {
-                    bfs_put(a, nlev, h.v, h.w[u], ce[u], cb[u], cx[u], at);
+                    bfs_put(a, nlev, h.v, h.w[u], ce[u], cb[u], cx[u], at, s_next, nbase);
                     ++at;
                 }
             }
             if (h.e > h.b + kSlotBatch)
-                bfs_place(a, nlev, h.v, plo + (int)threadIdx.x, h.b, h.b + kSlotBatch, h.e, mk0, at);
+                bfs_place(a, nlev, h.v, plo + (int)threadIdx.x, h.b, h.b + kSlotBatch, h.e, mk0, at, s_next, nbase);
         }
         int base_run = tot0;
         for (int c = 1; c < nchunk; ++c) {
@@ -332,22 +353,24 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
                 k = bfs_children(a, r, b, b, e, mk);
             }
             const int tot = bt_scan(k, excl);
-            if (k) bfs_place(a, nlev, p, r, b, b, e, mk, hi + before + base_run + excl);
+            if (k) bfs_place(a, nlev, p, r, b, b, e, mk, hi + before + base_run + excl, s_next, nbase);
             base_run += tot;
         }
         // the next set's parents of this CTA: its own children, or an even
         // split when the ownership is lopsided
         const int per = (total + CL - 1) / CL;
+        bool own = false;
         if (most - per > 64 || (most + BT - 1) / BT > (per + BT - 1) / BT) {
             cluster.sync();   // every CTA's children are written
             plo = min(hi + total, hi + crank * per);
             phi = min(hi + total, plo + per);
         } else {
-            __syncthreads();  // this CTA's children are written
-            plo = hi + before;
+            __syncthreads();  // this CTA's children are written (and their shared copies)
+            plo = nbase;
             phi = plo + mytotal;
+            own = true;
         }
-        bfs_offer_set(a, plo, phi, h);
+        bfs_offer_set(a, plo, phi, h, s_next, own);
         cluster.sync();
         if (crank == 0 && threadIdx.x == 0) a.lvl_off[nlev] = hi;
         ++nlev;
