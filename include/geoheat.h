@@ -250,11 +250,13 @@ gh_status gh_solve_batch(gh_mesh mesh, const int32_t *src_off, const int32_t *sr
  * Serving with continuous batching.  gh_submit queues one source set on a
  * loaded mesh and returns at once with a request id.  Worker threads of the
  * context (each with its own CUDA stream and workspaces) admit pending
- * requests as memory and batch slots free up, in arrival order, grouping
- * those that share the mesh and parameters, and run each group as one batch
- * (one breadth-first launch and one diffusion launch for all of it); requests
- * that arrive while others run join the next batch, and the workers' batches
- * overlap on the device.  A request's distances equal those of gh_solve with
+ * requests as memory and batch slots free up, in arrival order: the oldest
+ * pending request's precision and requests of similar work (vertices x
+ * sweeps within 4x of it), on any mesh and with any other parameters, run
+ * as one batch (one breadth-first launch and one diffusion launch for all of
+ * it; with gs_tol, one launch per round for the requests still running);
+ * requests that arrive while others run join the next batch, and the
+ * workers' batches overlap on the device.  A request's distances equal those of gh_solve with
  * the same arguments.  gh_submit, gh_poll and gh_wait are thread-safe.
  *
  * gh_serve_config: number of workers (1..8, default 2) and the batch limit

@@ -240,8 +240,9 @@ static gh_status run_diffusion(Ctx *c, std::vector<Item> &items, std::vector<Que
 
 // The whole path for a list of queries, each with its own mesh, workspace,
 // sources, parameters and (device) output; all of one precision.  One
-// breadth-first launch and one diffusion launch serve every query; the other
-// stages run per query.  stage_ms6 (may be null) gets the stage times.
+// breadth-first launch and one diffusion launch (one per round with gs_tol)
+// serve every query; the other stages run per query.  stage_ms6 (may be
+// null) gets the stage times.
 gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
     const int K = (int)items.size();
     gh_status s = GH_OK;

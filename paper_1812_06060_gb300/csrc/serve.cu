@@ -8,7 +8,8 @@
 // any parameters -- as long as their workspaces fit the memory budget (or
 // the device's free memory) and the batch limit, and runs them as one batch:
 // one breadth-first launch and one persistent diffusion launch for all of
-// them (every query with its own mesh and sweep count), then the per-query
+// them (every query with its own mesh and sweep count; with gs_tol, one
+// launch per round for the queries still running), then the per-query
 // stages.  Requests that arrive while a batch is on the GPU join the next
 // batch of whichever worker frees up first: one worker's breadth-first,
 // layout and ADMM work overlaps the other's diffusion, whose launch takes
