@@ -25,33 +25,74 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "geoheat_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libgeoheat_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libgeoheat_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_parallel = False
 
 MU = 100.0          # penalty parameter, Sec. 3.2 and Sec. 4.1
 ADMM_ITERS = 10     # I_max, Sec. 6
 ZERO_EXP = -(1 << 28)
 
 
+def _compile(target: str, extra: list, force: bool) -> str:
+    if force or not os.path.exists(target) or os.path.getmtime(target) < os.path.getmtime(_SRC):
+        tmp = target + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, target)
+    return target
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain IEEE double: no fast-math, no FMA
-    contraction) into oracle/_build."""
+    contraction) into oracle/_build: the single-threaded library and, from
+    the same source with -fopenmp, the level-parallel one."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    _compile(_LIB, [], force)
+    _compile(_LIB_OMP, ["-fopenmp"], force)
     return _LIB
 
 
 def lib():
-    global _lib
+    """The library the oracle functions call: the single-threaded one, or the
+    level-parallel one after set_parallel(True).  Both give bit-identical
+    results (tests/test_oracle_parallel.py)."""
+    key = bool(_parallel)
     with _lock:
-        if _lib is None:
-            _lib = C.CDLL(build())
-            _declare(_lib)
-    return _lib
+        if key not in _libs:
+            build()
+            L = C.CDLL(_LIB_OMP if key else _LIB)
+            _declare(L)
+            _libs[key] = L
+        return _libs[key]
+
+
+def set_parallel(on: bool) -> None:
+    """Select the level-parallel build (OpenMP on all the host's cores, or
+    OMP_NUM_THREADS of them) or the single-threaded one."""
+    global _parallel
+    _parallel = bool(on)
+
+
+class parallel:
+    """Context manager: the level-parallel build inside the block."""
+
+    def __init__(self, on: bool = True):
+        self.on = on
+
+    def __enter__(self):
+        self.prev = _parallel
+        set_parallel(self.on)
+        return self
+
+    def __exit__(self, *exc):
+        set_parallel(self.prev)
+
+
+def threads() -> int:
+    """Threads the selected build's parallel loops use (1 single-threaded)."""
+    return int(lib().orc_threads())
 
 
 P = C.c_void_p
@@ -61,6 +102,8 @@ D = C.c_double
 
 
 def _declare(L):
+    L.orc_threads.restype = C.c_int
+    L.orc_threads.argtypes = []
     L.orc_edges.restype = I64
     L.orc_edges.argtypes = [I64, I64, P, P]
     L.orc_connectivity.restype = C.c_int

@@ -7,9 +7,19 @@
  * the CPU-baseline leg of the benchmark may load this library.  It shares no
  * code, header, table or helper with the CUDA library it checks.
  *
- * Every function is a slow, single-threaded restatement of one step of the
- * paper, in the paper's order and notation, with no blocking or fusion.
- * Readings of passages the paper leaves open are marked READING.
+ * Every function is a slow restatement of one step of the paper, in the
+ * paper's order and notation, with no blocking or fusion.  Readings of
+ * passages the paper leaves open are marked READING.
+ *
+ * The same source builds two libraries: the plain one (compiled without
+ * OpenMP, where every `omp` pragma is ignored: single-threaded) and a
+ * level-parallel one (-fopenmp) for the large cases.  A pragma sits only on
+ * a loop whose iterations write disjoint locations and read nothing another
+ * iteration of the same loop writes -- the vertices of one breadth-first set
+ * in a Gauss-Seidel sweep (Jacobi within a set, eq. HeatDiffusionUpdate) or
+ * in the integration, the faces or edges of one ADMM block update -- and
+ * every sum whose value depends on its order stays a sequential loop, so the
+ * two libraries give bit-identical results.
  *
  * Numerical reading shared by the diffusion stages (READING, Sec. 3.1): the
  * heat solution u decays by roughly e^-1 per edge length away from the
@@ -25,6 +35,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORC_OK 0
 #define ORC_EINVAL (-1)
 #define ORC_ENOMEM (-2)
@@ -33,6 +47,15 @@
 /* exponent of an exact zero: far below any real exponent, and far enough
  * above INT32_MIN that differences of two exponents do not overflow */
 #define ORC_ZERO_EXP (-(1 << 28))
+
+/* threads the parallel loops use (1 in the plain build) */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Connectivity (Sec. 3 mesh (V, E, F); Sec. 4.1 orientation halfedges)      */
@@ -49,14 +72,17 @@ int64_t orc_edges(int64_t nv, int64_t nf, const int32_t *F, int32_t *edges_out) 
     if (nv <= 0 || nf <= 0) return ORC_EINVAL;
     int64_t *key = (int64_t *)malloc(sizeof(int64_t) * 3 * nf);
     if (!key) return ORC_ENOMEM;
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad)
     for (int64_t f = 0; f < nf; ++f) {
         for (int k = 0; k < 3; ++k) {
             int32_t a = F[3 * f + k], b = F[3 * f + (k + 1) % 3];
-            if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) { free(key); return ORC_EINVAL; }
+            if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) { bad = 1; key[3 * f + k] = 0; continue; }
             int32_t lo = a < b ? a : b, hi = a < b ? b : a;
             key[3 * f + k] = (int64_t)lo * nv + hi;
         }
     }
+    if (bad) { free(key); return ORC_EINVAL; }
     qsort(key, (size_t)(3 * nf), sizeof(int64_t), cmp_i64);
     int64_t ne = 0;
     for (int64_t i = 0; i < 3 * nf; ++i) {
@@ -108,15 +134,24 @@ int orc_connectivity(int64_t nv, int64_t nf, const int32_t *F, int64_t ne, const
                      const uint8_t *flip, int32_t *face_edge, int8_t *face_sign, int32_t *edge_face,
                      int32_t *edge_slot, int32_t *rowptr, int32_t *col, int32_t *col_edge) {
     for (int64_t e = 0; e < 2 * ne; ++e) { edge_face[e] = -1; edge_slot[e] = -1; }
+    int missing = 0;
+#pragma omp parallel for reduction(| : missing)
     for (int64_t f = 0; f < nf; ++f) {
         for (int k = 0; k < 3; ++k) {
             int32_t a = F[3 * f + (k + 1) % 3], b = F[3 * f + (k + 2) % 3]; /* loop a->b */
             int64_t e = find_edge(ne, edges, a, b);
-            if (e < 0) return ORC_EINVAL;
+            if (e < 0) { missing = 1; face_edge[3 * f + k] = -1; continue; }
             face_edge[3 * f + k] = (int32_t)e;
             int32_t t, h;
             eta(edges, flip, e, &t, &h);
             face_sign[3 * f + k] = (t == a && h == b) ? 1 : -1;
+        }
+    }
+    if (missing) return ORC_EINVAL;
+    /* the faces of each edge in ascending face order */
+    for (int64_t f = 0; f < nf; ++f) {
+        for (int k = 0; k < 3; ++k) {
+            int64_t e = face_edge[3 * f + k];
             if (edge_face[2 * e] < 0) { edge_face[2 * e] = (int32_t)f; edge_slot[2 * e] = k; }
             else if (edge_face[2 * e + 1] < 0) { edge_face[2 * e + 1] = (int32_t)f; edge_slot[2 * e + 1] = k; }
             else return ORC_ENONMANIFOLD;
@@ -144,6 +179,7 @@ int orc_connectivity(int64_t nv, int64_t nf, const int32_t *F, int64_t ne, const
         col[fill[b]] = a; col_edge[fill[b]++] = (int32_t)e;
     }
     free(fill);
+#pragma omp parallel for
     for (int64_t v = 0; v < nv; ++v) { /* insertion sort of each short row */
         for (int32_t i = rowptr[v] + 1; i < rowptr[v + 1]; ++i) {
             int32_t c = col[i], ce = col_edge[i], j = i - 1;
@@ -181,30 +217,36 @@ static double norm3(const double *a) { return sqrt(dot3(a, a)); }
 int orc_geometry(int64_t nv, const double *P, int64_t nf, const int32_t *F, int64_t ne, const int32_t *edges,
                  const int32_t *edge_face, const int32_t *edge_slot, double *Af, double *Av, double *cot,
                  double *theta, double *hbar) {
-    for (int64_t v = 0; v < nv; ++v) Av[v] = 0.0;
+#pragma omp parallel for
     for (int64_t f = 0; f < nf; ++f) {
         const double *p[3] = {P + 3 * F[3 * f], P + 3 * F[3 * f + 1], P + 3 * F[3 * f + 2]};
         double u[3], w[3], n[3];
         sub3(p[1], p[0], u);
         sub3(p[2], p[0], w);
         cross3(u, w, n);
-        double area = 0.5 * norm3(n);
-        Af[f] = area;
+        Af[f] = 0.5 * norm3(n);
         for (int k = 0; k < 3; ++k) {
             double a[3], b[3], c[3];
             sub3(p[(k + 1) % 3], p[k], a);
             sub3(p[(k + 2) % 3], p[k], b);
             cross3(a, b, c);
             cot[3 * f + k] = dot3(a, b) / norm3(c);
-            Av[F[3 * f + k]] += area / 3.0;
         }
     }
-    double sum = 0.0;
+    /* vertex areas: sums in face order */
+    for (int64_t v = 0; v < nv; ++v) Av[v] = 0.0;
+    for (int64_t f = 0; f < nf; ++f)
+        for (int k = 0; k < 3; ++k) Av[F[3 * f + k]] += Af[f] / 3.0;
+#pragma omp parallel for
     for (int64_t e = 0; e < ne; ++e) {
         double th = 0.0;
         for (int j = 0; j < 2; ++j)
             if (edge_face[2 * e + j] >= 0) th += 0.5 * cot[3 * edge_face[2 * e + j] + edge_slot[2 * e + j]];
         theta[e] = th;
+    }
+    /* mean edge length: the sum in edge order */
+    double sum = 0.0;
+    for (int64_t e = 0; e < ne; ++e) {
         double d[3];
         sub3(P + 3 * edges[2 * e], P + 3 * edges[2 * e + 1], d);
         sum += norm3(d);
@@ -295,6 +337,7 @@ int orc_gs(int64_t nv, const int32_t *rowptr, const int32_t *col, const int32_t 
     for (int32_t k = 0; k < sweeps; ++k) {
         for (int32_t i = 0; i < nlev; ++i) {
             /* new values of D_i into (nm, ne_), all from the state before D_i */
+#pragma omp parallel for if (level_off[i + 1] - level_off[i] > 256)
             for (int32_t q = level_off[i]; q < level_off[i + 1]; ++q) {
                 int32_t j = order[q];
                 double u0 = (i == 0) ? 1.0 : 0.0;
@@ -318,6 +361,7 @@ int orc_gs(int64_t nv, const int32_t *rowptr, const int32_t *col, const int32_t 
                 nm[j] = mm;
                 ne_[j] = (mm == 0.0) ? ORC_ZERO_EXP : ex + eref;
             }
+#pragma omp parallel for if (level_off[i + 1] - level_off[i] > 256)
             for (int32_t q = level_off[i]; q < level_off[i + 1]; ++q) {
                 int32_t j = order[q];
                 um[j] = nm[j];
@@ -391,6 +435,7 @@ double orc_heat_residual(int64_t nv, const int32_t *rowptr, const int32_t *col, 
 int orc_normalize(int64_t nv, const double *P, int64_t nf, const int32_t *F, const double *um, const int32_t *ue,
                   double *h) {
     (void)nv;
+#pragma omp parallel for
     for (int64_t f = 0; f < nf; ++f) {
         int32_t v[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
         const double *p[3] = {P + 3 * v[0], P + 3 * v[1], P + 3 * v[2]};
@@ -611,6 +656,7 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
 
     for (int32_t it = 0; it < iters; ++it) {
         /* Y-update, one interior edge at a time */
+#pragma omp parallel for
         for (int64_t e = 0; e < ne; ++e) {
             if (edge_face[2 * e + 1] < 0) continue;
             int64_t f1 = edge_face[2 * e], f2 = edge_face[2 * e + 1];
@@ -650,6 +696,7 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
         }
         /* G-update, one face at a time */
         for (int64_t i = 0; i < 3 * nf; ++i) gold[i] = g[i];
+#pragma omp parallel for
         for (int64_t f = 0; f < nf; ++f) {
             double alpha = sqrt(Af[f]);
             double acc[3] = {0, 0, 0};
@@ -663,7 +710,16 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
         }
         /* the multi-source path constraints, if any, as part of the G-update */
         pc_project(&pc, g);
-        /* lambda-update, and the residual norms */
+        /* lambda-update */
+#pragma omp parallel for
+        for (int64_t f = 0; f < nf; ++f) {
+            double alpha = sqrt(Af[f]);
+            for (int k = 0; k < 3; ++k) {
+                if (edge_face[2 * face_edge[3 * f + k] + 1] < 0) continue;
+                for (int c = 0; c < 3; ++c) lam[9 * f + 3 * k + c] += mu * (alpha * (y[9 * f + 3 * k + c] - g[3 * f + c]));
+            }
+        }
+        /* the residual norms, summed in slot order */
         double rp = 0.0, rd = 0.0;
         for (int64_t f = 0; f < nf; ++f) {
             double alpha = sqrt(Af[f]);
@@ -671,7 +727,6 @@ int orc_face_admm(int64_t nv, const double *P, int64_t nf, int64_t ne, const int
                 if (edge_face[2 * face_edge[3 * f + k] + 1] < 0) continue;
                 for (int c = 0; c < 3; ++c) {
                     double r = alpha * (y[9 * f + 3 * k + c] - g[3 * f + c]);
-                    lam[9 * f + 3 * k + c] += mu * r;
                     rp += r * r;
                     double dg = mu * alpha * (g[3 * f + c] - gold[3 * f + c]);
                     rd += dg * dg;
@@ -728,6 +783,7 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
     pc_factor(&pc);
     double *xold = (double *)malloc(sizeof(double) * (size_t)ne);
     if (!xold) { pc_free(&pc); return ORC_ENOMEM; }
+#pragma omp parallel for
     for (int64_t f = 0; f < nf; ++f) {
         for (int k = 0; k < 3; ++k) {
             if (z_in) {   /* targets given (an intrinsic triangulation's local frames) */
@@ -742,6 +798,7 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
             z[3 * f + k] = dot3(h + 3 * f, ev);
         }
     }
+#pragma omp parallel for
     for (int64_t e = 0; e < ne; ++e) {
         double s = 0.0;
         int n = 0;
@@ -758,6 +815,7 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
 
     for (int32_t it = 0; it < iters; ++it) {
         /* W-update per face */
+#pragma omp parallel for
         for (int64_t f = 0; f < nf; ++f) {
             double v[3], q[3];
             for (int k = 0; k < 3; ++k) {
@@ -768,6 +826,7 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
             for (int k = 0; k < 3; ++k) w[3 * f + k] = v[k] - q[k] * qv / 3.0;
         }
         /* X-update per edge */
+#pragma omp parallel for
         for (int64_t e = 0; e < ne; ++e) {
             xold[e] = x[e];
             double s = 0.0;
@@ -782,13 +841,16 @@ int orc_edge_admm(int64_t nv, const double *P, int64_t nf, const int32_t *F, int
         }
         /* the multi-source path constraints, if any, as part of the X-update */
         pc_project(&pc, x);
-        /* lambda-update per face slot, and the residual norms */
+        /* lambda-update per face slot */
+#pragma omp parallel for
+        for (int64_t f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) lam[3 * f + k] += mu * (w[3 * f + k] - x[face_edge[3 * f + k]]);
+        /* the residual norms, summed in slot order */
         double rp = 0.0, rd = 0.0;
         for (int64_t f = 0; f < nf; ++f) {
             for (int k = 0; k < 3; ++k) {
                 int64_t e = face_edge[3 * f + k];
                 double r = w[3 * f + k] - x[e];
-                lam[3 * f + k] += mu * r;
                 rp += r * r;
                 double d = mu * (x[e] - xold[e]);
                 rd += d * d;
@@ -831,10 +893,12 @@ int orc_integrate_face(int64_t nv, const double *P, const int32_t *rowptr, const
     for (int64_t v = 0; v < nv; ++v) d[v] = INFINITY;
     for (int32_t q = level_off[0]; q < level_off[1]; ++q) d[order[q]] = 0.0;
     for (int32_t i = 1; i < nlev; ++i) {
+        int missing = 0;
+#pragma omp parallel for reduction(| : missing) if (level_off[i + 1] - level_off[i] > 256)
         for (int32_t q = level_off[i]; q < level_off[i + 1]; ++q) {
             int32_t j = order[q], k = parent[j];
             int32_t e = csr_edge(rowptr, col, col_edge, k, j);
-            if (e < 0) return ORC_EINVAL;
+            if (e < 0) { missing = 1; continue; }
             double dp[3];
             sub3(P + 3 * j, P + 3 * k, dp);
             double s = 0.0;
@@ -852,6 +916,7 @@ int orc_integrate_face(int64_t nv, const double *P, const int32_t *rowptr, const
             }
             d[j] = d[k] + s / n;
         }
+        if (missing) return ORC_EINVAL;
     }
     return ORC_OK;
 }
@@ -868,14 +933,17 @@ int orc_integrate_edge(int64_t nv, const int32_t *edges, const uint8_t *flip, co
     for (int64_t v = 0; v < nv; ++v) d[v] = INFINITY;
     for (int32_t q = level_off[0]; q < level_off[1]; ++q) d[order[q]] = 0.0;
     for (int32_t i = 1; i < nlev; ++i) {
+        int missing = 0;
+#pragma omp parallel for reduction(| : missing) if (level_off[i + 1] - level_off[i] > 256)
         for (int32_t q = level_off[i]; q < level_off[i + 1]; ++q) {
             int32_t j = order[q], k = parent[j];
             int32_t e = csr_edge(rowptr, col, col_edge, k, j);
-            if (e < 0) return ORC_EINVAL;
+            if (e < 0) { missing = 1; continue; }
             int32_t ta, hd;
             eta(edges, flip, e, &ta, &hd);
             d[j] = (hd == j) ? d[k] + x[e] : d[k] - x[e];
         }
+        if (missing) return ORC_EINVAL;
     }
     return ORC_OK;
 }

@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, out):
 def test_replicas_two_ranks():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
     (s0, t0, v0), (s1, t1, v1) = out[0], out[1]
