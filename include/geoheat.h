@@ -322,19 +322,20 @@ gh_status gh_debug_dump(gh_mesh mesh, int32_t query, int32_t what, void *out);
 gh_status gh_stage_times(gh_mesh mesh, double *ms6);
 
 /*
- * Mean edge length (hbar of eq. DiffusionTime) of a mesh whose data the
- * caller already holds on the device, with no device allocation at all.  The
- * paper has no counterpart: this is a service for callers that cannot
- * allocate device memory, such as code running while a stream is captured
- * into a CUDA graph, applications whose own allocator owns all device memory,
- * or latency-critical paths where an allocation may synchronise the device.
- *  V       device, float64 [nv][3] vertex positions.
- *  edges   device, int32 [ne][2] vertex pairs, e.g. GH_DUMP_EDGES of a loaded
- *          mesh; every index must be inside V.
+ * Mean edge length of a mesh whose data the caller already holds on the
+ * device, with no device allocation at all.  The paper has no counterpart.
+ * It serves callers that cannot have a library allocate device memory:
+ * applications whose own allocator or memory pool owns the device memory
+ * and forbids other code from calling cudaMalloc, and latency-critical loops
+ * where a cudaMalloc or cudaFree may wait for the whole device to go idle.
+ *  V       device memory of the current device (or managed memory), float64
+ *          [nv][3] vertex positions.
+ *  edges   the same, int32 [ne][2] vertex pairs, e.g. GH_DUMP_EDGES of a
+ *          loaded mesh; every index must be inside V.
  *  ne      1 .. 536,870,912 edges (a fixed scratch of 8192 partial sums of
  *          65,536 edges each); larger counts return GH_EINVAL.
- *  out     device, float64 [1]: the mean edge length, the same two-level
- *          fixed-order sum as gh_mesh_load uses.
+ *  out     the same, float64 [1]: the mean edge length, the same two-level
+ *          fixed-order sum as gh_mesh_load uses (bit for bit).
  *  stream  cudaStream_t (NULL = legacy default stream); the call only
  *          enqueues two kernels and returns, out is ready when the stream
  *          reaches that point.
@@ -342,10 +343,11 @@ gh_status gh_stage_times(gh_mesh mesh, double *ms6);
  * loading the library holds until the process exits.  All calls on a device
  * share it, so calls whose kernels overlap on the GPU (different streams)
  * race; each call overwrites every partial it reads, so nothing needs
- * clearing.  The first call on a device looks the array's address up with
- * cudaGetSymbolAddress while that device is current; make that first call
- * before any stream capture.  Errors: GH_EINVAL (NULL or host pointer, ne out
- * of range), GH_EDEVICE.
+ * clearing.  The first call on a device (and the first after a device reset
+ * made a new context) looks the array's address up with cudaGetSymbolAddress
+ * while that device is current; make that first call before any stream
+ * capture.  Errors: GH_EINVAL (NULL pointer, host memory or memory of
+ * another device, ne out of range), GH_EDEVICE.
  */
 gh_status gh_mean_edge_length_noalloc(const double *V, const int32_t *edges, int64_t ne, double *out, void *stream);
 

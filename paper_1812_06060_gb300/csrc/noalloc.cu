@@ -3,14 +3,15 @@
 // gh_mesh_load computes the mean edge length hbar (the length scale of the
 // diffusion time t = m hbar^2) with a two-level deterministic reduction whose
 // per-block partial sums live in memory it allocates.  This file holds a
-// variant of that reduction for callers that must not allocate device memory
-// themselves or through the library: code that runs while a CUDA stream is
-// being captured into a graph (allocation calls are not allowed there),
-// applications that hand every byte of the device to their own allocator and
-// forbid others from calling cudaMalloc, and real-time paths where an
-// allocation may block on a device-wide synchronisation.  The partial sums
-// live in a fixed file-scope device array instead.
+// variant of that reduction for callers that cannot have the library
+// allocate device memory: applications whose own allocator or memory pool
+// owns the device memory and forbids other code from calling cudaMalloc (a
+// renderer or a framework with its own caching allocator, a process that has
+// reserved nearly all of the device), and latency-critical loops where a
+// cudaMalloc or cudaFree may wait for the whole device to go idle.  The
+// partial sums live in a fixed file-scope device array instead.
 #include <mutex>
+#include <string>
 
 #include "internal.cuh"
 
@@ -64,32 +65,64 @@ __global__ void __launch_bounds__(kNaThreads) k_na_final(const double *__restric
     if (threadIdx.x == 0) out[0] = s[0] / (double)ne;
 }
 
-bool on_device(const void *p) {
+// true for device memory of the current device (or managed memory, which
+// the current device can reach)
+bool on_current_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// Id of the current context (cuCtxGetId through the runtime's driver entry
+// points, so the library needs no link to the driver library), 0 if the
+// driver cannot tell.  A context made after a device reset has a new id.
+unsigned long long current_context_id() {
+    typedef int (*get_current_fn)(void **);
+    typedef int (*get_id_fn)(void *, unsigned long long *);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<get_id_fn>(f);
+        (void)cudaGetLastError();
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device.  In host code g_na_partials names a host-side stand-in, not
-// device memory, so kernels get the address from cudaGetSymbolAddress.
-gh_status na_scratch(double **out) {
+// per device and context.  In host code g_na_partials names a host-side
+// stand-in, not device memory, so kernels get the address from
+// cudaGetSymbolAddress, called while that device is current.
+gh_status na_scratch(int dev, double **out) {
     static std::mutex mu;
     static double *addr[kNaMaxDevices] = {};
-    int dev = 0;
-    GH_CUDA(cudaGetDevice(&dev));
+    static unsigned long long ctx_of[kNaMaxDevices] = {};
     if (dev < 0 || dev >= kNaMaxDevices) {
         set_error("device ordinal out of range for the fixed scratch table");
         return GH_EINVAL;
     }
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || ctx_of[dev] != ctx) {
         double *p = nullptr;
         GH_CUDA(cudaGetSymbolAddress((void **)&p, g_na_partials));
         addr[dev] = p;
+        ctx_of[dev] = ctx;
     }
     *out = addr[dev];
     return GH_OK;
@@ -111,12 +144,14 @@ extern "C" gh_status gh_mean_edge_length_noalloc(const double *V, const int32_t 
                   std::to_string((int64_t)kNaMaxParts * kNaPerBlock) + " edges");
         return GH_EINVAL;
     }
-    if (!on_device(V) || !on_device(edges) || !on_device(out)) {
-        set_error("V, edges and out must be device memory of the current device");
+    int dev = 0;
+    GH_CUDA(cudaGetDevice(&dev));
+    if (!on_current_device(V, dev) || !on_current_device(edges, dev) || !on_current_device(out, dev)) {
+        set_error("V, edges and out must be device memory of the current device (" + std::to_string(dev) + ")");
         return GH_EINVAL;
     }
     double *part = nullptr;
-    gh_status s = na_scratch(&part);
+    gh_status s = na_scratch(dev, &part);
     if (s != GH_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_na_partial<<<(unsigned)nb, kNaThreads, 0, st>>>(V, edges, ne, part);
