@@ -435,6 +435,21 @@ def workload_c5(level: int = 12) -> Workload:
     return Workload(f"sinusoid_ico{level}", mesh, [src], m=10.0, gs_face=2000, gs_edge=4000, forms=("edge",))
 
 
+def serving_sweeps(mesh: Mesh) -> int:
+    """Sweep count of a serving mesh: about twice its breadth-first depth, the
+    count at which breadth-first Gauss-Seidel has converged (grid side N:
+    depth <= N; icosphere level n: depth <= 3 * 2^n)."""
+    if "N" in mesh.meta:
+        return 2 * int(mesh.meta["N"])
+    return 6 * (1 << int(mesh.meta["level"]))
+
+
+def serving_request(k: int, mesh: Mesh) -> np.ndarray:
+    """The seeded request (1..16 uniform sources) whose oracle distances are
+    stored for serving mesh k."""
+    return random_sources(rng_for(config_seed(4, 300 + k)), mesh.nv, 1, 16)
+
+
 def serving_meshes() -> list[Mesh]:
     """The ten meshes of the serving stream: jittered grids of side 101, 257,
     513, 1025, 2000 and noisy icospheres of level 5..9."""

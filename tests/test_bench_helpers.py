@@ -9,10 +9,21 @@ import bench
 
 
 def test_diffusion_bytes_are_the_per_unit_figures_times_the_units():
-    # 1025^2 grid: 1,050,625 vertices, 3,147,776 edges, 2000 sweeps; 24 bytes per
-    # vertex-sweep and 8 per directed edge
-    assert bench.gs_bytes(1_050_625, 3_147_776, 2000) == 2000 * (24 * 1_050_625 + 8 * 2 * 3_147_776)
-    assert bench.gs_bytes(1_050_625, 3_147_776, 2000) == 151_158_832_000
+    # 16 V + 16 E per sweep: per vertex a row pointer, the diagonal, u read and
+    # written (4 each); per directed edge (2E) a column index and a weight (8)
+    assert bench.gs_bytes(1_050_625, 3_147_776, 2000) == 2000 * (16 * 1_050_625 + 8 * 2 * 3_147_776)
+    assert bench.gs_bytes(1_050_625, 3_147_776, 2000) == 134_348_832_000
+    # the 168M-vertex mesh: 4000 x (16 x 167,772,162 + 16 x 503,316,480) = 42.95 TB per launch
+    assert bench.gs_bytes(167_772_162, 503_316_480, 4000) == 42_949_673_088_000
+    # the library's 8-byte state adds 8 bytes per vertex-sweep
+    assert bench.gs_state_bytes(1_050_625, 2000) == 2000 * 8 * 1_050_625
+
+
+def test_traffic_scales_with_vertex_sweeps():
+    cap = {"dram_bytes_per_launch": 1.0e9, "vertex_sweeps": 2_621_442 * 100}
+    t = bench.scaled_traffic(cap, 167_772_162, 4000)
+    assert math.isclose(t, 1.0e9 * 167_772_162 * 4000 / (2_621_442 * 100))
+    assert bench.scaled_traffic(None, 10, 10) is None
 
 
 def test_stage_bytes():
@@ -39,7 +50,8 @@ def test_capture_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
            "gs_cu_sha256": hashlib.sha256(b"// kernel v1\n").hexdigest()}
     (tmp_path / "profiles" / "k_gs_grid1025.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.gs_traffic() == 123.0
-    assert bench.gs_capture()["lts_bytes"] == 456.0
+    assert bench.capture("k_gs_grid1025")["dram_bytes_per_full_launch"] == 123.0
+    assert bench.capture("k_gs_grid1025")["lts_bytes"] == 456.0
+    assert bench.capture("k_gs_sinusoid_ico9") is None
     (src / "gs.cu").write_bytes(b"// kernel v2\n")
-    assert bench.gs_traffic() is None and bench.gs_capture() is None
+    assert bench.capture("k_gs_grid1025") is None
