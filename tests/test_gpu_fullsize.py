@@ -184,7 +184,8 @@ def test_c5_full_size_against_oracle(gh):
     ctx = gh.Context(0)
     M = gh.Mesh(ctx, mesh.V, mesh.F)
     try:
-        assert abs(M.hbar - md.hbar) <= 1e-12 * md.hbar
+        # two sums of ne positive lengths in different orders: within 2 ne 2^-53
+        assert abs(M.hbar - md.hbar) <= 2 * md.ne * 2.0 ** -53 * md.hbar
         # (1) the whole path in FP64 at 10 sweeps
         with oracle.parallel(True):
             ref = oracle.solve(md, src, "edge", sweeps=10, m=w.m)
