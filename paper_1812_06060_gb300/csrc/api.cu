@@ -178,7 +178,10 @@ gh_status validate_params(const gh_params *p) {
 size_t ws_bytes(const DevMesh &m, int fp64, int form, int path_constraints) {
     const size_t es = fp64 ? 8 : 4, xs = fp64 ? 16 : 8;
     size_t nv = m.nv, nf = m.nf, ne = m.ne;
-    size_t b = nv * (6 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) + es * 3 * nf;
+    // the level-ordered operator with a quarter more for the padding of its
+    // tiles (a tile's rows are padded to its longest row)
+    size_t b = nv * (6 * 4 + 8 + 4 + 4 + es + 8 + 4 + 2 * xs + 8 + 16 + 8) + 2 * ne * (fp64 ? 16 : 8) * 5 / 4 +
+               es * 3 * nf;
     b += (form == GH_FORM_FACE) ? es * 24 * nf : es * (9 * nf + 2 * ne);
     // path constraints: the block's variable map and an allowance for the entries
     // (sources x sets; their allocations are checked against the budget anyway)

@@ -485,7 +485,7 @@ __global__ void k_split_scatter(const int32_t *__restrict__ order, int n, const 
 
 // widest row of each tile (one warp per tile); wsize[t] = W * cp
 __global__ void k_tile_width(const int32_t *__restrict__ ptile, int n_even, int n_odd, int tiles_cap,
-                             const int32_t *__restrict__ len, TileDesc *tiles, int32_t *wsize) {
+                             const int32_t *__restrict__ len, TileDesc *tiles, int32_t *wsize, int32_t *maxw) {
     const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (t >= tiles_cap) return;
     const int ntiles = ptile[n_even] + ptile[n_even + 1 + n_odd];
@@ -500,6 +500,7 @@ __global__ void k_tile_width(const int32_t *__restrict__ ptile, int n_even, int 
     if (lane == 0) {
         tiles[t].ee = w;
         wsize[t] = w * ((count + 31) & ~31);
+        atomicMax(maxw, w);
     }
 }
 
@@ -783,10 +784,14 @@ gh_status build_layout(Ctx *c, const DevMesh &m, QueryWs &q, double t) {
     k_tiles<<<1, BT, 0, st>>>(ptr<int32_t>(q.lvl_off), q.nlev, ptr<int32_t>(q.ptile), ptr<TileDesc>(q.tiles)); ++c->launches;
     const int n_even = (q.nlev + 1) / 2, n_odd = q.nlev / 2;
     int32_t *wsize = ptr<int32_t>(q.twid), *eoff = wsize + tiles_cap + 1;
+    int32_t *maxw_dev = ptr<int32_t>(q.meta) + 3;
+    GH_CUDA(cudaMemsetAsync(maxw_dev, 0, sizeof(int32_t), st));
     k_tile_width<<<blocks_for((int64_t)tiles_cap * 32, 256), 256, 0, st>>>(ptr<int32_t>(q.ptile), n_even, n_odd,
                                                                        (int)tiles_cap, len, ptr<TileDesc>(q.tiles),
-                                                                       wsize); ++c->launches;
+                                                                       wsize, maxw_dev); ++c->launches;
     GH_CUDA(cudaGetLastError());
+    // read back with the scan's total (the scan waits for the stream)
+    GH_CUDA(cudaMemcpyAsync(&q.max_w, maxw_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     int32_t total = 0;
     if ((s = exclusive_scan_i32(c, wsize, eoff, (int64_t)tiles_cap, &total)) != GH_OK) return s;
     const size_t es = q.fp64 ? sizeof(Ent<double>) : sizeof(Ent<float>);

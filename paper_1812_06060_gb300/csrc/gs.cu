@@ -55,7 +55,7 @@ namespace gh {
 namespace {
 
 constexpr unsigned long long kWaitTimeoutNs = 2000000000ull;  // 2 s for a staging-barrier wait
-constexpr int kMaxDeg = 8;                                    // row entries held in registers
+constexpr int kMaxDeg = 8;                                    // row entries held in registers (wide stages)
 
 template <class T> struct GsJob {
     int nlev;
@@ -241,19 +241,28 @@ __device__ bool wait_sets(const int32_t *p0, int t0, const int32_t *p1, int t1, 
 constexpr int kCW = 8;                        // consumer warps per CTA
 constexpr int kThreads = 32 * (kCW + 1);      // + one producer warp
 constexpr int kVPT = TILE / (32 * kCW);       // positions per consumer thread
-constexpr int kEntStage = kMaxDeg * TILE;     // staged row entries (wider tiles read their rows from global)
 static_assert(kVPT * 32 * kCW == TILE, "tile must split evenly over the consumer threads");
 
-// one staging buffer: the tile's row pointers, diagonal and rows, plus the
-// tile's facts written by the producer
-template <class T> struct alignas(128) Stage {
-    Ent<T> ent[kEntStage];
+// one staging buffer: the tile's diagonal and rows (up to MAXD entries per
+// row; wider tiles read their rows from global memory), plus the tile's
+// facts written by the producer
+template <class T, int MAXD> struct alignas(128) Stage {
+    Ent<T> ent[MAXD * TILE];
     T diag[TILE + 8];
     int start, count, lo, k, level, cp, w, d0, e0, fits, abort, finished, q, pad[3];
 };
 // every bulk-copy destination must start on a 16-byte boundary, in both stages
-static_assert(sizeof(Stage<float>) % 16 == 0 && sizeof(Stage<double>) % 16 == 0, "stage size");
-static_assert(offsetof(Stage<float>, diag) % 16 == 0 && offsetof(Stage<double>, diag) % 16 == 0, "stage layout");
+static_assert(sizeof(Stage<float, 8>) % 16 == 0 && sizeof(Stage<double, 8>) % 16 == 0, "stage size");
+static_assert(sizeof(Stage<float, 6>) % 16 == 0, "stage size");
+using StageF8 = Stage<float, 8>;
+using StageD8 = Stage<double, 8>;
+using StageF6 = Stage<float, 6>;
+static_assert(offsetof(StageF8, diag) % 16 == 0 && offsetof(StageD8, diag) % 16 == 0 &&
+              offsetof(StageF6, diag) % 16 == 0, "stage layout");
+
+// resident CTAs per SM: FP32 with 8-entry stages 3 (shared memory and 72
+// registers), with 6-entry stages 4 (56 registers); FP64 1
+template <class T, int MAXD> constexpr int gs_ctas_per_sm() { return sizeof(T) == 4 ? (MAXD <= 6 ? 4 : 3) : 1; }
 
 constexpr int kMaxJobs = 256;                 // queries per launch (larger batches take several launches)
 
@@ -285,7 +294,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // The rows of one tile (consumer warp cw's positions), the first D entries of
 // each row held in registers; entries past D (tiles wider than kMaxDeg only)
 // are read one at a time.  Ucur / Uprv: this and the previous sweep's state.
-template <class T, int D>
+template <class T, int D, bool WIDE = true>
 __device__ __forceinline__ void gs_tile_rows(XVal<T> *Ucur, const XVal<T> *Uprv, const Ent<T> *E, const T *sdiag,
                                              int zero_pos, int start, int count, int lo, int cp, int wt, int sd,
                                              int cw, int lane) {
@@ -311,7 +320,7 @@ __device__ __forceinline__ void gs_tile_rows(XVal<T> *Ucur, const XVal<T> *Uprv,
         int eref = (lo == 0) ? 1 : kZeroExp;   // zero states carry kZeroExp: no test needed
 #pragma unroll
         for (int a = 0; a < D; ++a) eref = max(eref, u[v][a].e);
-        for (int a = D; a < wt; ++a) {  // rows longer than D (tiles wider than kMaxDeg)
+        for (int a = D; WIDE && a < wt; ++a) {  // rows longer than D (tiles wider than kMaxDeg)
             const Ent<T> x = E[a * cp + p];
             const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
             if (w.m != T(0)) eref = max(eref, w.e);
@@ -322,7 +331,7 @@ __device__ __forceinline__ void gs_tile_rows(XVal<T> *Ucur, const XVal<T> *Uprv,
             const T w = (a < wt) ? E[a * cp + p].w : T(0);
             acc += w * xscale(u[v][a].m, u[v][a].e - eref);
         }
-        for (int a = D; a < wt; ++a) {
+        for (int a = D; WIDE && a < wt; ++a) {
             const Ent<T> x = E[a * cp + p];
             const XVal<T> w = ld_state((x.col < lo ? Ucur : Uprv) + x.col);
             acc += x.w * xscale(w.m, w.e - eref);
@@ -340,12 +349,13 @@ __device__ __forceinline__ void gs_tile_rows(XVal<T> *Ucur, const XVal<T> *Uprv,
 // state, update and store; the last warp of the tile to finish adds one to
 // the set's counter with a release add, so a set of nt tiles is complete for
 // sweep k once its counter reaches (k + 1) * nt.
-template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
+template <class T, int MAXD>
+__global__ void __launch_bounds__(kThreads, (gs_ctas_per_sm<T, MAXD>()))
     k_gs(const GsJob<T> *__restrict__ jobs, int njobs, int nrounds, unsigned long long wait_limit_ns,
          int *abort_flag, int *status) {
+    constexpr int kEntStage = MAXD * TILE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Stage<T> *stage = reinterpret_cast<Stage<T> *>(smem_raw);
+    Stage<T, MAXD> *stage = reinterpret_cast<Stage<T, MAXD> *>(smem_raw);
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ int scur_job[kMaxJobs];   // producer: step cursor of each query
     for (int q = threadIdx.x; q < njobs; q += blockDim.x) scur_job[q] = 0;
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                 int ok = 1;
                 if (lane == 0) {
                     const int b = j & 1;
-                    Stage<T> &S = stage[b];
+                    Stage<T, MAXD> &S = stage[b];
                     // predecessors: (k, i-1), (k-1, i), (k-1, i+1); their counters are
                     // read now, so the loads are in flight while the buffer frees up
                     const int i = d.level, k = (s - d.level) >> 1;
@@ -458,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         if ((cand / njobs) * grid + cta >= jobs[cand % njobs].ntickets) continue;
         const int b = j & 1;
         ++j;
-        Stage<T> &S = stage[b];
+        Stage<T, MAXD> &S = stage[b];
         if (!mbar_wait_bounded(&full[b], fph[b], abort_flag)) {
             if (lane == 0) {
                 atomicExch(abort_flag, 1);
@@ -478,10 +488,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
         // the tile's width picks how many entries of a row sit in registers,
         // so a tile of short rows does no arithmetic on padding (the skipped
         // terms are exact zeros: the result is the same)
+        if (MAXD <= 6 && wt > MAXD) {
+            // the host launches 6-entry stages only when no tile is wider
+            if (lane == 0) {
+                atomicExch(abort_flag, 1);
+                atomicCAS(status, DEV_OK, DEV_EINTERNAL);
+            }
+            return;
+        }
         if (wt <= 4)
-            gs_tile_rows<T, 4>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
-        else if (wt <= 6)
-            gs_tile_rows<T, 6>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
+            gs_tile_rows<T, 4, (MAXD > 6)>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
+        else if (MAXD <= 6 || wt <= 6)
+            gs_tile_rows<T, 6, (MAXD > 6)>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
         else
             gs_tile_rows<T, kMaxDeg>(Ucur, Uprv, E, S.diag, J.zero_pos, start, count, lo, cp, wt, sd, cw, lane);
         __syncwarp();
@@ -526,9 +544,15 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cu
     cudaStream_t st = c->stream;
     const int K = (int)ws.size();
     int per_sm = 0;
-    const size_t smem = 2 * sizeof(Stage<T>);
-    GH_CUDA(cudaFuncSetAttribute(k_gs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs<T>, kThreads, smem));
+    // 6-entry stages (4 resident CTAs per SM) when no tile of the launch is
+    // wider than 6 entries (the icosphere meshes), else 8-entry stages (3)
+    int maxw = 0;
+    for (QueryWs *w : ws) maxw = std::max(maxw, w->max_w);
+    const bool narrow = sizeof(T) == 4 && maxw <= 6;
+    void *kfn = narrow ? (void *)k_gs<T, 6> : (void *)k_gs<T, kMaxDeg>;
+    const size_t smem = narrow ? 2 * sizeof(Stage<T, 6>) : 2 * sizeof(Stage<T, kMaxDeg>);
+    GH_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem));
     if (per_sm < 1) { set_error("diffusion kernel does not fit on an SM"); return GH_EDEVICE; }
     const int grid = std::max(1, per_sm * c->num_sms / std::max(1, c->gs_share));
     std::vector<GsJob<T>> jobs(K);
@@ -597,7 +621,7 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cu
     void *argv[] = {(void *)&djobs,         (void *)&njobs,      (void *)&nrounds,
                     (void *)&wait_limit_ns, (void *)&abort_flag, (void *)&status};
     if (ev0) cudaEventRecord(ev0, st);
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_gs<T>, dim3(grid), dim3(kThreads), argv, smem, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads), argv, smem, st);
     ++c->launches;
     if (ev1) cudaEventRecord(ev1, st);
     cudaFreeAsync(djobs, st);

@@ -24,6 +24,7 @@
 #include <mutex>
 #include <stdexcept>
 #include <thread>
+#include <tuple>
 
 #include "internal.cuh"
 
@@ -45,7 +46,6 @@ struct Request {
 
 struct Worker {
     Ctx c;
-    std::map<DevMesh *, std::vector<QueryWs *>> pools;   // workspaces kept per mesh
     DBuf dout;
     std::thread th;
 };
@@ -59,6 +59,10 @@ struct Engine {
     gh_req next_id = 1;
     bool stop = false;
     int max_batch = 32;
+    int running = 0;                                      // workers with a batch on the GPU
+    size_t reserved = 0;                                  // bytes admitted batches may still allocate
+    // workspaces no batch is using, per (mesh, form, precision) of their last request
+    std::map<std::tuple<DevMesh *, int, int>, std::vector<QueryWs *>> idle;
     std::vector<Worker *> workers;
 };
 
@@ -76,54 +80,125 @@ gh_ctx_s *gh_mesh_ctx(gh_mesh_s *m);
 
 namespace gh {
 
+// device bytes a new batch may take (E->mu held): the budget less what the
+// context holds, or 80% of the device's free memory without a budget, less
+// what the batches admitted earlier may still allocate (a batch allocates
+// after it leaves the lock, so its admitted bytes stay reserved until its
+// solve has returned)
+static size_t avail_bytes(Engine *E, Ctx *c) {
+    Shared *sh = c->shared;
+    size_t a;
+    if (sh->budget) {
+        size_t used = sh->in_use.load();
+        a = sh->budget > used ? sh->budget - used : 0;
+    } else {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        a = (size_t)(0.8 * (double)fr);
+    }
+    return a > E->reserved ? a - E->reserved : 0;
+}
+
+// frees idle workspaces (E->mu held) until `need` bytes are available or
+// none is left; returns the bytes available afterwards
+static size_t release_idle(Engine *E, Worker *W, size_t need) {
+    size_t avail = avail_bytes(E, &W->c);
+    for (auto it = E->idle.begin(); it != E->idle.end() && avail < need;) {
+        std::vector<QueryWs *> &v = it->second;
+        while (!v.empty() && avail < need) {
+            free_ws(&W->c, v.back());
+            delete v.back();
+            v.pop_back();
+            avail = avail_bytes(E, &W->c);
+        }
+        it = v.empty() ? E->idle.erase(it) : std::next(it);
+    }
+    return avail;
+}
+
 static void worker_loop(Engine *E, Worker *W) {
     cudaSetDevice(W->c.device);
     while (true) {
         std::vector<Request *> batch;
         std::vector<QueryWs *> wsq;
+        size_t batch_cost = 0;
         {
             std::unique_lock<std::mutex> lk(E->mu);
-            E->cv_work.wait(lk, [&] { return E->stop || !E->pending.empty(); });
-            if (E->stop && E->pending.empty()) return;
-            const int fp64 = E->pending.front()->p.fp64;
-            auto work = [](const Request *r) {
-                return (double)gh_mesh_host(r->mesh)->m.nv * (double)std::max(1, r->p.gs_sweeps);
-            };
-            const double w0 = work(E->pending.front());
-            // admission in arrival order: a workspace this worker already holds
-            // for the request's mesh costs nothing, a new one its size
-            size_t avail;
-            Shared *sh = W->c.shared;
-            if (sh->budget) {
-                size_t used = sh->in_use.load();
-                avail = sh->budget > used ? sh->budget - used : 0;
-            } else {
-                size_t fr = 0, tot = 0;
-                cudaMemGetInfo(&fr, &tot);
-                avail = (size_t)(0.8 * (double)fr);
-            }
-            std::map<DevMesh *, size_t> taken;
-            for (auto it = E->pending.begin(); it != E->pending.end() && (int)batch.size() < E->max_batch;) {
-                Request *r = *it;
-                const double wr = work(r);
-                if (r->p.fp64 != fp64 || wr > 4.0 * w0 || 4.0 * wr < w0) {
-                    ++it;
+            while (true) {
+                E->cv_work.wait(lk, [&] { return E->stop || !E->pending.empty(); });
+                if (E->stop && E->pending.empty()) return;
+                const int fp64 = E->pending.front()->p.fp64;
+                auto work = [](const Request *r) {
+                    return (double)gh_mesh_host(r->mesh)->m.nv * (double)std::max(1, r->p.gs_sweeps);
+                };
+                const double w0 = work(E->pending.front());
+                // admission in arrival order: an idle workspace of the request's
+                // mesh costs nothing, a new one its size (plus the growth of this
+                // worker's output buffer); a request that does not fit waits
+                size_t avail = avail_bytes(E, &W->c);
+                size_t out_bytes = 0;
+                batch_cost = 0;
+                std::map<std::tuple<DevMesh *, int, int>, size_t> taken;
+                for (auto it = E->pending.begin(); it != E->pending.end() && (int)batch.size() < E->max_batch;) {
+                    Request *r = *it;
+                    const double wr = work(r);
+                    if (r->p.fp64 != fp64 || wr > 4.0 * w0 || 4.0 * wr < w0) {
+                        ++it;
+                        continue;
+                    }
+                    DevMesh *m = &gh_mesh_host(r->mesh)->m;
+                    const auto key = std::make_tuple(m, r->p.form, fp64);
+                    const size_t k = taken[key];
+                    auto idl = E->idle.find(key);
+                    const bool reuse = idl != E->idle.end() && k < idl->second.size();
+                    const size_t ob = out_bytes + sizeof(double) * (size_t)m->nv;
+                    const size_t grow = ob > W->dout.bytes ? ob - std::max(out_bytes, W->dout.bytes) : 0;
+                    const size_t cost = (reuse ? 0 : ws_bytes(*m, fp64, r->p.form, r->p.path_constraints)) + grow;
+                    if (cost > avail) {
+                        if (!batch.empty()) break;   // the rest waits for the next batch
+                        avail = release_idle(E, W, cost);
+                        if (cost > avail) break;     // the oldest request waits for memory
+                    }
+                    avail -= cost;
+                    batch_cost += cost;
+                    out_bytes = ob;
+                    taken[key] = k + 1;
+                    batch.push_back(r);
+                    r->state = 1;
+                    it = E->pending.erase(it);
+                }
+                if (!batch.empty()) break;
+                // nothing fits: wait for a running batch to give memory back; with
+                // none running (and every idle workspace freed) the oldest
+                // request can never fit and fails
+                if (E->running == 0) {
+                    Request *r = E->pending.front();
+                    E->pending.pop_front();
+                    r->status = GH_ENOMEM;
+                    r->err = "the request's workspace does not fit the context's device memory budget";
+                    r->state = 2;
+                    gh_mesh_host(r->mesh)->inflight.fetch_sub(1);
+                    E->cv_done.notify_all();
                     continue;
                 }
-                DevMesh *m = &gh_mesh_host(r->mesh)->m;
-                std::vector<QueryWs *> &pool = W->pools[m];
-                const size_t k = taken[m];
-                const bool reuse = k < pool.size() && pool[k]->level.p;
-                const size_t cost = reuse ? 0 : ws_bytes(*m, fp64, r->p.form, r->p.path_constraints);
-                if (!batch.empty() && cost > avail) break;   // the rest waits for memory
-                avail -= std::min(cost, avail);
-                if (k == pool.size()) pool.push_back(new QueryWs());
-                taken[m] = k + 1;
-                wsq.push_back(pool[k]);
-                batch.push_back(r);
-                r->state = 1;
-                it = E->pending.erase(it);
+                E->cv_work.wait(lk);
             }
+            // the batch's workspaces: idle ones of its meshes first, then new ones
+            for (Request *r : batch) {
+                auto idl = E->idle.find(std::make_tuple(&gh_mesh_host(r->mesh)->m, r->p.form, r->p.fp64));
+                if (idl != E->idle.end() && !idl->second.empty()) {
+                    wsq.push_back(idl->second.back());
+                    idl->second.pop_back();
+                    if (idl->second.empty()) E->idle.erase(idl);
+                } else {
+                    wsq.push_back(new QueryWs());
+                }
+            }
+            ++E->running;
+            E->reserved += batch_cost;
         }
         gh_status st = GH_OK;
         std::string err;
@@ -143,6 +218,12 @@ static void worker_loop(Engine *E, Worker *W) {
             st = GH_EDEVICE;
             err = std::string("serving worker: ") + ex.what();
         }
+        {
+            // the batch's allocations are done (or failed): its reservation ends
+            std::lock_guard<std::mutex> lk(E->mu);
+            E->reserved -= std::min(E->reserved, batch_cost);
+        }
+        E->cv_work.notify_all();
         if (st == GH_OK) {
             try {
                 for (size_t q = 0; q < batch.size(); ++q) batch[q]->d.resize(off[q + 1] - off[q]);
@@ -164,14 +245,19 @@ static void worker_loop(Engine *E, Worker *W) {
         }
         {
             std::lock_guard<std::mutex> lk(E->mu);
-            for (Request *r : batch) {
+            for (size_t q = 0; q < batch.size(); ++q) {
+                E->idle[std::make_tuple(&gh_mesh_host(batch[q]->mesh)->m, batch[q]->p.form, batch[q]->p.fp64)]
+                    .push_back(wsq[q]);
+                Request *r = batch[q];
                 r->status = st;
                 r->err = err;
                 r->state = 2;
                 gh_mesh_host(r->mesh)->inflight.fetch_sub(1);
             }
+            --E->running;
         }
         E->cv_done.notify_all();
+        E->cv_work.notify_all();   // memory came back: a waiting admission may fit now
     }
 }
 
@@ -211,13 +297,15 @@ void engine_stop(Engine *E) {
         E->stop = true;
     }
     E->cv_work.notify_all();
-    for (Worker *W : E->workers) {
+    for (Worker *W : E->workers)
         if (W->th.joinable()) W->th.join();
-        for (auto &kv : W->pools)
-            for (QueryWs *w : kv.second) {
-                free_ws(&W->c, w);
-                delete w;
-            }
+    for (auto &kv : E->idle)
+        for (QueryWs *w : kv.second) {
+            free_ws(&E->workers[0]->c, w);
+            delete w;
+        }
+    E->idle.clear();
+    for (Worker *W : E->workers) {
         dfree(&W->c, W->dout);
         cudaStreamDestroy(W->c.stream);
         cudaFree(W->c.status_dev);
@@ -232,14 +320,16 @@ void engine_stop(Engine *E) {
 // the workers keep for it.
 void engine_forget_mesh(Engine *E, DevMesh *m) {
     std::lock_guard<std::mutex> lk(E->mu);
-    for (Worker *W : E->workers) {
-        auto it = W->pools.find(m);
-        if (it == W->pools.end()) continue;
+    for (auto it = E->idle.begin(); it != E->idle.end();) {
+        if (std::get<0>(it->first) != m || E->workers.empty()) {
+            ++it;
+            continue;
+        }
         for (QueryWs *w : it->second) {
-            free_ws(&W->c, w);
+            free_ws(&E->workers[0]->c, w);
             delete w;
         }
-        W->pools.erase(it);
+        it = E->idle.erase(it);
     }
 }
 

@@ -481,19 +481,25 @@ PcDev pc_dev(const QueryWs &q) {
 // increment of each vertex over its breadth-first pairing vertex k:
 // face form  1/|T| sum_{f in T_jk} g_f . (p_j - p_k)   (eq. IntegrationStep)
 // edge form  +x_e if v_j is the head of the orientation halfedge, else -x_e
+// The increment of each reached vertex over its pairing vertex, in layout
+// order: position r holds vertex v = lorder[r].  The chains of pairing
+// vertices then run from a set to the previous one, whose positions lie
+// close together, so the pointer-jumping rounds below gather nearly
+// contiguous data.  nxt[r] is the position of the pairing vertex (-1 on the
+// sources); d[r] starts as the increment.
 template <class T>
-__global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, const int32_t *__restrict__ parent,
+__global__ void k_increments(int nr, const int32_t *__restrict__ lorder, const int32_t *__restrict__ pos,
+                             const int32_t *__restrict__ level, const int32_t *__restrict__ parent,
                              const int32_t *__restrict__ pedge, const int32_t *__restrict__ edges,
                              const int32_t *__restrict__ edge_face, const double *__restrict__ P,
-                             const T *__restrict__ g, const T *__restrict__ x, int form, double *inc, int32_t *nxt,
-                             double *d, const int32_t *__restrict__ edge_slot, const double *__restrict__ evf) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    int lv = level[v];
-    if (lv <= 0) {
-        inc[v] = 0.0;
-        nxt[v] = -1;
-        d[v] = (lv == 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
+                             const T *__restrict__ g, const T *__restrict__ x, int form, int32_t *nxt, double *d,
+                             const int32_t *__restrict__ edge_slot, const double *__restrict__ evf) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    const int v = lorder[r];
+    if (level[v] == 0) {
+        nxt[r] = -1;
+        d[r] = 0.0;
         return;
     }
     const int p = parent[v];
@@ -501,13 +507,13 @@ __global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, cons
     double dv;
     if (form == GH_FORM_EDGE) {
         double xe = (double)x[e];
-        dv = (edges[2 * e + 1] == (int)v) ? xe : -xe;
+        dv = (edges[2 * e + 1] == v) ? xe : -xe;
     } else {
         double dp[3] = {0.0, 0.0, 0.0};
         if (!evf) {
-            dp[0] = P[3 * v] - P[3 * p];
-            dp[1] = P[3 * v + 1] - P[3 * p + 1];
-            dp[2] = P[3 * v + 2] - P[3 * p + 2];
+            dp[0] = P[3 * (int64_t)v] - P[3 * (int64_t)p];
+            dp[1] = P[3 * (int64_t)v + 1] - P[3 * (int64_t)p + 1];
+            dp[2] = P[3 * (int64_t)v + 2] - P[3 * (int64_t)p + 2];
         }
         double s = 0.0;
         int n = 0;
@@ -516,17 +522,26 @@ __global__ void k_increments(int64_t nv, const int32_t *__restrict__ level, cons
             if (f < 0) continue;
             if (evf) {   // an intrinsic triangulation: p_v - p_p in face f's frame, its slot vector
                 const double *sv = evf + 9 * (int64_t)f + 3 * edge_slot[2 * e + a];
-                const double sg = ((int)v > p) ? 1.0 : -1.0;
+                const double sg = (v > p) ? 1.0 : -1.0;
                 dp[0] = sg * sv[0]; dp[1] = sg * sv[1]; dp[2] = sg * sv[2];
             }
-            s += (double)g[3 * f] * dp[0] + (double)g[3 * f + 1] * dp[1] + (double)g[3 * f + 2] * dp[2];
+            s += (double)g[3 * (int64_t)f] * dp[0] + (double)g[3 * (int64_t)f + 1] * dp[1] +
+                 (double)g[3 * (int64_t)f + 2] * dp[2];
             ++n;
         }
         dv = s / n;
     }
-    inc[v] = dv;
-    nxt[v] = p;
-    d[v] = dv;
+    nxt[r] = pos[p];
+    d[r] = dv;
+}
+
+// the distances in vertex order: +infinity where no source reaches
+__global__ void k_gather_d(int64_t nv, const int32_t *__restrict__ pos, const double *__restrict__ dpos,
+                           double *d) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int r = pos[v];
+    d[v] = (r >= 0) ? dpos[r] : __longlong_as_double(0x7ff0000000000000ll);
 }
 
 // Sum of the increments along each vertex's chain of pairing vertices by
@@ -703,24 +718,28 @@ template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, i
 
 template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, double *d_out) {
     cudaStream_t st = c->stream;
-    unsigned nb = blocks_for(m.nv, NT);
-    double *d[2] = {ptr<double>(q.d0), ptr<double>(q.d1)};
+    const int nr = q.nreach;
+    // position-ordered chains ping-pong between (inc, n0) and (d1, n1); the
+    // result goes to d0 in vertex order (read by gh_debug_dump)
+    double *d[2] = {ptr<double>(q.inc), ptr<double>(q.d1)};
     int32_t *n[2] = {ptr<int32_t>(q.n0), ptr<int32_t>(q.n1)};
-    k_increments<T><<<nb, NT, 0, st>>>(m.nv, ptr<int32_t>(q.level), ptr<int32_t>(q.parent), ptr<int32_t>(q.pedge),
-                                       ptr<int32_t>(m.edges),
-                                       ptr<int32_t>(m.edge_face), ptr<double>(m.P), ptr<T>(q.g0), ptr<T>(q.x), q.form,
-                                       ptr<double>(q.inc), n[0], d[0], ptr<int32_t>(m.edge_slot),
-                                       m.intrinsic ? ptr<double>(m.evf64) : nullptr); ++c->launches;
+    if (nr > 0) {
+        k_increments<T><<<blocks_for(nr, NT), NT, 0, st>>>(
+            nr, ptr<int32_t>(q.lorder), ptr<int32_t>(q.pos), ptr<int32_t>(q.level), ptr<int32_t>(q.parent),
+            ptr<int32_t>(q.pedge), ptr<int32_t>(m.edges), ptr<int32_t>(m.edge_face), ptr<double>(m.P),
+            ptr<T>(q.g0), ptr<T>(q.x), q.form, n[0], d[0], ptr<int32_t>(m.edge_slot),
+            m.intrinsic ? ptr<double>(m.evf64) : nullptr); ++c->launches;
+    }
     int rounds = 0;
     while ((1 << rounds) < q.nlev) ++rounds;
     int cur = 0;
-    for (int r = 0; r < rounds; ++r) {
-        k_jump<<<nb, NT, 0, st>>>(m.nv, d[cur], n[cur], d[cur ^ 1], n[cur ^ 1]); ++c->launches;
+    for (int r = 0; r < rounds && nr > 0; ++r) {
+        k_jump<<<blocks_for(nr, NT), NT, 0, st>>>(nr, d[cur], n[cur], d[cur ^ 1], n[cur ^ 1]); ++c->launches;
         cur ^= 1;
     }
-    // the workspace keeps the result in d0 (read by gh_debug_dump)
-    if (cur == 1) GH_CUDA(cudaMemcpyAsync(d[0], d[1], sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
-    if (d_out) GH_CUDA(cudaMemcpyAsync(d_out, d[0], sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
+    k_gather_d<<<blocks_for(m.nv, NT), NT, 0, st>>>(m.nv, ptr<int32_t>(q.pos), d[cur], ptr<double>(q.d0));
+    ++c->launches;
+    if (d_out) GH_CUDA(cudaMemcpyAsync(d_out, ptr<double>(q.d0), sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
     GH_CUDA(cudaGetLastError());
     return GH_OK;
 }

@@ -134,3 +134,67 @@ def test_serving_errors(gh):
     assert e.value.status == gh.GH_EBUSY
     M.close()
     ctx.close()
+
+
+def test_admission_waits_for_memory_across_meshes(gh):
+    """Two workers, three meshes and a budget with room for the meshes and
+    less than two query workspaces: a request whose workspace does not fit
+    waits until memory comes back (idle workspaces of other meshes are
+    released), and every request is served, bit-equal to its solo solve."""
+    meshes = [meshgen.jittered_grid(129, 61), meshgen.noisy_icosphere(5, 62), meshgen.jittered_grid(121, 63)]
+    prm = gh.params(gs_sweeps=120, form="edge")
+    rng = meshgen.rng_for(64)
+    reqs = [(k % 3, meshgen.random_sources(rng, meshes[k % 3].nv, 1, 6)) for k in range(18)]
+    free_ctx = gh.Context(0)
+    mesh_bytes, ws_max, solo = 0, 0, []
+    Ms = []
+    for m in meshes:
+        before = free_ctx.memory()
+        Ms.append(gh.Mesh(free_ctx, m.V, m.F))
+        mesh_bytes += free_ctx.memory() - before
+    for k, M in enumerate(Ms):
+        before = free_ctx.memory()
+        out = np.empty(meshes[k].nv)
+        M.solve([1], out, prm)
+        ws_max = max(ws_max, free_ctx.memory() - before)
+    for k, s_ in reqs:
+        out = np.empty(meshes[k].nv)
+        Ms[k].solve(s_, out, prm)
+        solo.append(out)
+    for M in Ms:
+        M.close()
+    free_ctx.close()
+    budget = int(mesh_bytes + 1.5 * ws_max)
+    ctx = gh.Context(0, hbm_budget=budget)
+    ctx.serve_config(workers=2, max_batch=8)
+    M = [gh.Mesh(ctx, m.V, m.F) for m in meshes]
+    ids = [ctx.submit(M[k], s_, prm) for k, s_ in reqs]
+    for (k, _), ref, rid in zip(reqs, solo, ids):
+        out = np.empty(meshes[k].nv)
+        ctx.wait(rid, out)   # raises on any status but GH_OK
+        assert np.array_equal(out, ref)
+    assert ctx.memory() <= budget
+    for m in M:
+        m.close()
+    ctx.close()
+
+
+def test_request_that_can_never_fit_fails(gh):
+    """With room for the mesh but not for one query workspace, a served
+    request returns GH_ENOMEM (it would never fit) instead of waiting."""
+    mesh = meshgen.jittered_grid(129, 65)
+    probe = gh.Context(0)
+    Mp = gh.Mesh(probe, mesh.V, mesh.F)
+    mesh_bytes = probe.memory()
+    Mp.close()
+    probe.close()
+    # the mesh's setup needs about a sixth more than it keeps; a query
+    # workspace needs more than half the mesh again
+    ctx = gh.Context(0, hbm_budget=int(mesh_bytes * 1.3))
+    M = gh.Mesh(ctx, mesh.V, mesh.F)
+    rid = ctx.submit(M, [3], gh.params(gs_sweeps=50, form="edge"))
+    with pytest.raises(gh.GeoheatError) as e:
+        ctx.wait(rid, np.empty(mesh.nv), timeout_us=30_000_000)
+    assert e.value.status == gh.GH_ENOMEM
+    M.close()
+    ctx.close()
