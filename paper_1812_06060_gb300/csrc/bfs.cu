@@ -40,6 +40,10 @@ struct BfsArgs {
     int32_t ntargets;
 };
 
+// the second level of this scan is one warp over the warps' totals: exactly
+// 32 warps, one per lane (every lane reads and writes its entry of ws)
+static_assert(BT == 1024, "bt_scan's second level assumes 32 warps per CTA");
+
 __device__ int32_t bt_scan(int32_t v, int32_t &excl) {
     __shared__ int32_t ws[BT / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
