@@ -468,6 +468,17 @@ def run_ours(args):
                                        "the breadth-first stage is bound by its L dependent set steps, not HBM"},
             "clocks": clk.summary(),
         }
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "c5":
+        # the same mesh with t = hbar^2 (m = 1), same sweeps: one timed solve
+        p1 = g.params(gs_sweeps=sweeps, admm_iters=ADMM, form=forms[0], m=1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M.solve(src, out[forms[0]], p1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        result["extra_m1"] = {"workload": desc.replace(f"m = {m}", "m = 1.0"), "solve_ms": e0.elapsed_time(e1),
+                              "solves_per_s": 1000.0 / e0.elapsed_time(e1),
+                              "stage_ms": dict(zip(list(STAGES) + ["k_gs"], [round(x, 4) for x in M.stage_times()]))}
     M.close()
     ctx.close()
     del out, src
