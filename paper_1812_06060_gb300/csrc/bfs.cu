@@ -245,7 +245,7 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
     const int crank = (int)cluster.block_rank();
     // the arguments stay in shared memory: registers go to the held rows
     __shared__ BfsArgs s_args;
-    __shared__ int s_total;
+    __shared__ int s_tot[CL];   // this set's children per CTA of the cluster
     __shared__ NextRow s_next[BT];
     if (threadIdx.x == 0) s_args = all[blockIdx.x / CL];
     __syncthreads();
@@ -301,13 +301,15 @@ template <int CL> __global__ void __launch_bounds__(BT, 1) k_bfs(const BfsArgs *
             if (c == 0) { k0 = k; ex0 = excl; tot0 = tot; mk0 = mk; }
             mytotal += tot;
         }
-        if (threadIdx.x == 0) s_total = mytotal;
+        // every CTA's total goes to every CTA's shared memory before the
+        // barrier (remote stores; the barrier publishes them), so after it the
+        // totals are local: lane q of every warp reads CTA q's, shuffles sum them
+        if ((int)threadIdx.x < CL) *cluster.map_shared_rank(&s_tot[crank], (int)threadIdx.x) = mytotal;
         cluster.sync();
-        // lane q of every warp reads CTA q's total; shuffles sum them
         int before, total, most;
         {
             const int lane = (int)(threadIdx.x & 31);
-            const int t = lane < CL ? *cluster.map_shared_rank(&s_total, lane) : 0;
+            const int t = lane < CL ? s_tot[lane] : 0;
             before = lane < crank ? t : 0;
             total = t;
             most = t;
