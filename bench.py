@@ -538,17 +538,19 @@ def c2_summary(g, device, peak, peak_kind, steps=3):
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for f in C2_FORMS:
         M.solve(src, out, prm[f])
-    gs_ms, total = [], 0.0
+    gs_ms, total, st = [], 0.0, {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(steps):
         flush.zero_()
         e0.record(stream)
         for f in C2_FORMS:
             M.solve(src, out, prm[f])
-            gs_ms.append(M.stage_times()[5])
+            st[f] = M.stage_times()
+            gs_ms.append(st[f][5])
         e1.record(stream)
         torch.cuda.synchronize()
         total += e0.elapsed_time(e1)
+    nlev = len(M.dump(g.GH_DUMP_LEVEL_OFF)) - 1
     nb = gs_bytes(mesh.nv, M.ne, C2_SWEEPS)
     avg = statistics.mean(gs_ms)
     ach = nb / (avg / 1000.0) / 1e9
@@ -556,7 +558,11 @@ def c2_summary(g, device, peak, peak_kind, steps=3):
     res = {"workload": f"jittered grid 1025x1025 ({mesh.nv} V), one source, {C2_SWEEPS} sweeps, face + edge forms",
            "solves_per_s": len(C2_FORMS) * steps / (total / 1000.0), "steps": steps,
            "l2": "flushed (512 MiB write) before every step",
-           "roofline": c2_roofline(capture("k_gs_grid1025"), nb, avg, peak, peak_kind, ach, ws)}
+           "roofline": c2_roofline(capture("k_gs_grid1025"), nb, avg, peak, peak_kind, ach, ws),
+           "stage_roofline": {"peak_GBps": peak, "note": "last step's stage times; algorithmic bytes",
+                              "by_form": {f: stage_roofline(st[f], stage_bytes(mesh.nv, M.ne, mesh.nf, C2_SWEEPS,
+                                                                                ADMM, f, nlev), peak)
+                                          for f in C2_FORMS}}}
     M.close()
     ctx.close()
     return res

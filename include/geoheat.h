@@ -113,6 +113,14 @@ typedef enum { GH_FORM_FACE = 0, GH_FORM_EDGE = 1 } gh_form;
  *              gh_debug_dump (GH_DUMP_GS_SWEEPS).  0 (the default): exactly
  *              gs_sweeps sweeps.  Must be finite and >= 0.
  *  gs_check    sweeps per E1 evaluation when gs_tol > 0; >= 1.  Default 100.
+ *  gs_band     the order in which the pipelined sweeps run; the result is the
+ *              same, bit for bit, for every value.  The sweeps run in bands
+ *              of gs_band sweeps, one after the other, each band a wavefront
+ *              over the breadth-first sets, so fewer sets are in flight at a
+ *              time and more of a step's reads are found in L2.  0 (the
+ *              default): chosen from the layout, one band (the plain
+ *              wavefront) unless the sets hold many tiles (on a 168M-vertex
+ *              mesh, about 200 sweeps).  Must be >= 0.
  */
 typedef struct {
     double m;
@@ -130,6 +138,7 @@ typedef struct {
     int32_t cycle_constraints;
     double gs_tol;
     int32_t gs_check;
+    int32_t gs_band;
 } gh_params;
 
 /* Fills *p with the defaults listed above. */

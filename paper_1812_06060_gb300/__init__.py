@@ -45,7 +45,7 @@ class GhParams(C.Structure):
                 ("mu", C.c_double), ("form", C.c_int32), ("fp64", C.c_int32), ("diagnostics", C.c_int32),
                 ("early_stop", C.c_int32), ("eps1", C.c_double), ("eps2", C.c_double),
                 ("path_constraints", C.c_int32), ("cycle_constraints", C.c_int32), ("gs_tol", C.c_double),
-                ("gs_check", C.c_int32)]
+                ("gs_check", C.c_int32), ("gs_band", C.c_int32)]
 
 
 class GeoheatError(RuntimeError):
@@ -129,12 +129,14 @@ def _check(rc: int):
 
 
 def params(m=1.0, t=0.0, gs_sweeps=200, admm_iters=10, mu=100.0, form="edge", fp64=False, diagnostics=False,
-           eps=None, path_constraints=False, cycle_constraints=False, gs_tol=0.0, gs_check=100):
+           eps=None, path_constraints=False, cycle_constraints=False, gs_tol=0.0, gs_check=100, gs_band=0):
     """Solver parameters; eps = (eps1, eps2) turns on early termination of the
     ADMM; path_constraints adds the multi-source path constraints,
     cycle_constraints the cycle constraints of a closed mesh of genus >= 1;
     gs_tol > 0 ends the diffusion once the heat residual E1 is within it
-    (checked every gs_check sweeps, at most gs_sweeps)."""
+    (checked every gs_check sweeps, at most gs_sweeps); gs_band sets the
+    sweeps per band of the pipelined diffusion (0: chosen from the layout;
+    the result is the same for every value)."""
     p = GhParams()
     lib().gh_params_default(C.byref(p))
     p.m, p.t, p.gs_sweeps, p.admm_iters, p.mu = m, t, gs_sweeps, admm_iters, mu
@@ -145,6 +147,7 @@ def params(m=1.0, t=0.0, gs_sweeps=200, admm_iters=10, mu=100.0, form="edge", fp
     p.path_constraints = int(bool(path_constraints))
     p.cycle_constraints = int(bool(cycle_constraints))
     p.gs_tol, p.gs_check = float(gs_tol), int(gs_check)
+    p.gs_band = int(gs_band)
     return p
 
 

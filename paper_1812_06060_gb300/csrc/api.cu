@@ -171,6 +171,7 @@ gh_status validate_params(const gh_params *p) {
     }
     if (!(p->gs_tol >= 0 && p->gs_tol < 1e300)) { set_error("gs_tol must be finite and >= 0"); return GH_EINVAL; }
     if (p->gs_tol > 0 && p->gs_check < 1) { set_error("gs_check must be >= 1 when gs_tol > 0"); return GH_EINVAL; }
+    if (p->gs_band < 0) { set_error("gs_band must be >= 0"); return GH_EINVAL; }
     return GH_OK;
 }
 
@@ -214,6 +215,7 @@ static gh_status run_diffusion(Ctx *c, std::vector<Item> &items, std::vector<Que
         for (int q : active) {
             const gh_params *p = items[q].p;
             ws[q]->sweeps = (p->gs_tol > 0) ? std::min(p->gs_check, left[q]) : left[q];
+            ws[q]->gs_band = p->gs_band;
             run.push_back(ws[q]);
         }
         gh_status s = run_gs(c, run, first ? ev0 : nullptr, nullptr);
@@ -450,6 +452,7 @@ void gh_params_default(gh_params *p) {
     p->cycle_constraints = 0;
     p->gs_tol = 0.0;
     p->gs_check = 100;
+    p->gs_band = 0;
 }
 
 const char *gh_version(void) { return "geoheat 0.1 (sm_103a)"; }

@@ -46,6 +46,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 
 #include "internal.cuh"
@@ -59,8 +60,10 @@ constexpr int kMaxDeg = 8;                                    // row entries hel
 
 template <class T> struct GsJob {
     int nlev;
-    int nsteps;            // nlev + 2 (sweeps - 1)
+    int nsteps;            // nbands * band_steps
     int nsweeps;           // this query's sweeps
+    int band;              // sweeps per band
+    int band_steps;        // steps per band: nlev + 2 (band - 1)
     int n_even;            // number of even sets; ptile0[n_even] = first tile of the odd sets
     int ntickets;          // tiles over all steps
     int zero_pos;          // a position that always holds the zero state (nreach)
@@ -150,16 +153,29 @@ __device__ __forceinline__ XVal<double> ld_state(const XVal<double> *p) {
     return x;
 }
 
-// tile range [first, first + count) of job j at step s
-template <class T> __device__ __forceinline__ void step_range(const GsJob<T> &j, int s, int &first,
+// Steps run band by band: band b holds sweeps [b * band, b * band + kb) and
+// band_steps steps; its step s (global step b * band_steps + s) covers the
+// pairs (k, i) with 2 (k - b * band) + i = s.  One band of all sweeps is the
+// plain wavefront.
+__device__ __forceinline__ void step_band(int g, int band_steps, int band, int &s, int &k0) {
+    const int b = g / band_steps;
+    s = g - b * band_steps;
+    k0 = b * band;
+}
+
+// tile range [first, first + count) of job j at global step g
+template <class T> __device__ __forceinline__ void step_range(const GsJob<T> &j, int g, int &first,
                                                              int &count) {
     first = 0;
     count = 0;
-    if (s >= j.nsteps) return;
+    if (g >= j.nsteps) return;
+    int s, k0;
+    step_band(g, j.band_steps, j.band, s, k0);
+    const int kb = min(j.band, j.nsweeps - k0);
     int p = s & 1;
     int ihi = min(j.nlev - 1, s);
     if ((ihi & 1) != p) --ihi;
-    int ilo = max(p, s - 2 * (j.nsweeps - 1));
+    int ilo = max(p, s - 2 * (kb - 1));
     if (ilo > ihi) return;
     int jlo = (ilo - p) >> 1, jhi = (ihi - p) >> 1;
     const int32_t *pt = p ? j.ptile1 : j.ptile0;
@@ -416,7 +432,9 @@ __global__ void __launch_bounds__(kThreads, (gs_ctas_per_sm<T, MAXD>()))
                     Stage<T, MAXD> &S = stage[b];
                     // predecessors: (k, i-1), (k-1, i), (k-1, i+1); their counters are
                     // read now, so the loads are in flight while the buffer frees up
-                    const int i = d.level, k = (s - d.level) >> 1;
+                    int sb, k0;
+                    step_band(s, J.band_steps, J.band, sb, k0);
+                    const int i = d.level, k = k0 + ((sb - d.level) >> 1);
                     const int t0 = (i > 0) ? (k + 1) * d.nt_prev : 0;
                     const int t1 = (k > 0) ? k * d.nt_self : 0;
                     const int t2 = (k > 0) ? k * d.nt_next : 0;
@@ -528,6 +546,23 @@ template <class T> __global__ void k_zero_state(XVal<T> *a, XVal<T> *b, int n) {
     }
 }
 
+// Sweeps per band.  A step of the plain wavefront holds a tile of up to
+// half the sets (every set of its parity that some sweep is at), so on a
+// mesh much larger than L2 a set's state and rows are evicted between one
+// sweep's use and the next one's.  Bands of K sweeps hold K sets per step;
+// K is chosen so that a step still has about kBandTiles tiles (its work then
+// stays far above the latency of one dependent step), and bands are used
+// only when there are four or more of them.
+constexpr double kBandTiles = 6500.0;
+
+int gs_band(const QueryWs &w) {
+    const int all = std::max(1, w.sweeps);
+    if (w.gs_band > 0) return std::min(w.gs_band, all);
+    const double tiles_per_set = ((double)w.nreach / TILE + w.nlev) / std::max(1, w.nlev);
+    const int band = (int)std::ceil(kBandTiles / tiles_per_set);
+    return (4.0 * band <= all) ? band : all;
+}
+
 template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cudaEvent_t ev0,
                                      cudaEvent_t ev1) {
     if ((int)all_ws.size() > kMaxJobs) {   // one launch per kMaxJobs queries
@@ -558,7 +593,10 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cu
     std::vector<GsJob<T>> jobs(K);
     std::vector<int> prev_buf(K);
     size_t soff_total = 0;
-    for (int q = 0; q < K; ++q) soff_total += (size_t)ws[q]->nlev + 2 * (size_t)ws[q]->sweeps + 2;
+    for (int q = 0; q < K; ++q) {
+        const int band = gs_band(*ws[q]);
+        soff_total += (size_t)((ws[q]->sweeps + band - 1) / band) * (size_t)(ws[q]->nlev + 2 * (band - 1)) + 2;
+    }
     int32_t *scratch = nullptr;   // per query: step counts and their prefix
     GH_CUDA(cudaMallocAsync((void **)&scratch, sizeof(int32_t) * 2 * soff_total, st));
     GsJob<T> *djobs = nullptr;
@@ -568,8 +606,10 @@ template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cu
         QueryWs &w = *ws[q];
         GsJob<T> j{};
         j.nlev = w.nlev;
-        j.nsteps = w.nlev + 2 * (w.sweeps - 1);
         j.nsweeps = w.sweeps;
+        j.band = gs_band(w);
+        j.band_steps = w.nlev + 2 * (j.band - 1);
+        j.nsteps = ((w.sweeps + j.band - 1) / j.band) * j.band_steps;
         j.n_even = (w.nlev + 1) / 2;
         j.lvl_off = ptr<int32_t>(w.lvl_off);
         j.gent = ptr<Ent<T>>(w.gent);

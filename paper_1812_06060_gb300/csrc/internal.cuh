@@ -208,6 +208,7 @@ struct QueryWs {
     int nlev = 0, nreach = 0, final_buf = 0, form = 1, admm_iters = 0, diagnostics = 0, sweeps = 0;
     int max_w = 8;         // widest row block of the layout (entries per row)
     int gs_continue = 0;   // 1: the next diffusion launch resumes from the state of the last one
+    int gs_band = 0;       // sweeps per band of the next diffusion launch (0: from the layout)
     int sweeps_run = 0;    // sweeps of the last solve (all rounds)
     double t = 0.0;
 };

@@ -338,6 +338,9 @@ def test_errors(gh, ctx):
     with pytest.raises(gh.GeoheatError) as e:
         M.solve(np.array([0], np.int32), d, gh.params(gs_sweeps=0))
     assert e.value.status == gh.GH_EINVAL
+    with pytest.raises(gh.GeoheatError) as e:
+        M.solve(np.array([0], np.int32), d, gh.params(gs_band=-1))
+    assert e.value.status == gh.GH_EINVAL
     for kind, cl in ((0, 7), (2, 8), (-1, 16), (1, 32)):
         with pytest.raises(gh.GeoheatError) as e:
             M.set_tuning(kind, cl)
