@@ -49,7 +49,7 @@ ADMM = 10
 C2_SWEEPS = 2000
 C2_FORMS = ("face", "edge")
 SAMPLE_LEVEL = 9          # the oracle's bounded sample: the level-9 mesh of the benchmark's family
-SAMPLE_SWEEPS = 100       # Gauss-Seidel sweeps of the sample (scaled to the full count)
+SAMPLE_SWEEPS = 400       # Gauss-Seidel sweeps of the sample (scaled to the full count): about 10 s on 16 cores
 E2E_MAX_STEPS = 3         # end-to-end steps (each copies the 1.3 GB distance field back to the host)
 
 
