@@ -555,12 +555,24 @@ template <class T> __global__ void k_zero_state(XVal<T> *a, XVal<T> *b, int n) {
 // only when there are four or more of them.
 constexpr double kBandTiles = 6500.0;
 
+// Bands of K sweeps take ceil(N / K) (L + 2 (K - 1)) steps; a band is widened
+// (doubled) until that is at most kMaxSteps, which bounds the step table
+// (8 bytes per step) whatever gs_band asks for.
+constexpr long long kMaxSteps = 1ll << 26;
+
 int gs_band(const QueryWs &w) {
     const int all = std::max(1, w.sweeps);
-    if (w.gs_band > 0) return std::min(w.gs_band, all);
-    const double tiles_per_set = ((double)w.nreach / TILE + w.nlev) / std::max(1, w.nlev);
-    const int band = (int)std::ceil(kBandTiles / tiles_per_set);
-    return (4.0 * band <= all) ? band : all;
+    int band;
+    if (w.gs_band > 0) {
+        band = std::min(w.gs_band, all);
+    } else {
+        const double tiles_per_set = ((double)w.nreach / TILE + w.nlev) / std::max(1, w.nlev);
+        band = (int)std::ceil(kBandTiles / tiles_per_set);
+        band = (4.0 * band <= all) ? band : all;
+    }
+    while (band < all && (long long)((all + band - 1) / band) * (w.nlev + 2ll * (band - 1)) > kMaxSteps)
+        band = (int)std::min<long long>(2ll * band, all);
+    return band;
 }
 
 template <class T> gh_status run_gs_t(Ctx *c, std::vector<QueryWs *> &all_ws, cudaEvent_t ev0,
