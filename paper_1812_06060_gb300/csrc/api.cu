@@ -319,7 +319,7 @@ gh_status solve_items(Ctx *c, std::vector<Item> &items, double *stage_ms6) {
 // gets K x nv.  Queries go in passes of as many as the budget (or 80% of
 // free memory) allows, at most 64.
 gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
-                     const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k) {
+                     const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k, double *d_out_host) {
     const int K = (int)src.size();
     size_t per = ws_bytes(m, p->fp64, p->form, p->path_constraints);
     size_t avail;
@@ -343,6 +343,13 @@ gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std
         for (int q = 0; q < kq; ++q)
             items[q] = Item{&m, pool[q], &src[q0 + q], p, d_out_dev ? d_out_dev + (size_t)(q0 + q) * m.nv : nullptr};
         s = solve_items(c, items, ms);
+        // host output: straight from each workspace's distances (the next
+        // chunk reuses the workspaces only after these copies, in stream order)
+        for (int q = 0; q < kq && s == GH_OK && d_out_host; ++q) {
+            cudaError_t e = cudaMemcpyAsync(d_out_host + (size_t)(q0 + q) * m.nv, pool[q]->d0.p,
+                                            sizeof(double) * (size_t)m.nv, cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) s = cuda_fail(e, "copy of the distances to the host");
+        }
     }
     if (s == GH_OK) {
         if (last_k) *last_k = std::min(K, chunk);
@@ -352,10 +359,10 @@ gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std
 }
 
 static gh_status solve_impl(gh_mesh_s *mh, const std::vector<std::vector<int32_t>> &src, const gh_params *p,
-                            double *d_out_dev) {
+                            double *d_out_dev, double *d_out_host = nullptr) {
     double ms6[6];
     int lk = 0;
-    gh_status s = solve_core(&mh->ctx->c, mh->h.m, mh->h.ws, src, p, d_out_dev, ms6, &lk);
+    gh_status s = solve_core(&mh->ctx->c, mh->h.m, mh->h.ws, src, p, d_out_dev, ms6, &lk, d_out_host);
     if (s == GH_OK) {
         mh->h.last_k = lk;
         std::copy(ms6, ms6 + 5, mh->h.stage_ms);
@@ -391,17 +398,10 @@ gh_status prep_sources(const int32_t *src, int32_t nsrc, int64_t nv, std::vector
 static gh_status solve_to(gh_mesh_s *mh, const std::vector<std::vector<int32_t>> &sets, const gh_params *p,
                           double *d_out) {
     Ctx *c = &mh->ctx->c;
-    const size_t bytes = sizeof(double) * (size_t)mh->h.m.nv * sets.size();
     if (is_device_ptr(d_out)) return solve_impl(mh, sets, p, d_out);
-    double *tmp = nullptr;
-    GH_CUDA(cudaMallocAsync((void **)&tmp, bytes, c->stream));
-    gh_status s = solve_impl(mh, sets, p, tmp);
-    if (s == GH_OK) {
-        cudaError_t e = cudaMemcpyAsync(d_out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) s = cuda_fail(e, "copy of the distances to the host");
-    }
-    cudaFreeAsync(tmp, c->stream);
+    gh_status s = solve_impl(mh, sets, p, nullptr, d_out);
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (s == GH_OK && e != cudaSuccess) s = cuda_fail(e, "copy of the distances to the host");
     return s;
 }
 

@@ -225,9 +225,12 @@ struct MeshH {
 
 // The whole path for a list of source sets on one mesh, with the launcher
 // context `c` and the workspace pool `pool` (grown as needed).  d_out_dev:
-// device, [K][nv] (may be null).  stage_ms6 (may be null) gets the stage times.
+// device, [K][nv] (may be null); d_out_host: host, [K][nv] (may be null),
+// each query's distances copied there from its workspace, in stream order
+// (the caller synchronises).  stage_ms6 (may be null) gets the stage times.
 gh_status solve_core(Ctx *c, DevMesh &m, std::vector<QueryWs *> &pool, const std::vector<std::vector<int32_t>> &src,
-                     const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k);
+                     const gh_params *p, double *d_out_dev, double *stage_ms6, int *last_k,
+                     double *d_out_host = nullptr);
 
 // One query of a heterogeneous batch.
 struct Item {

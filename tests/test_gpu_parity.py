@@ -295,6 +295,29 @@ def test_batch_equals_single_solves(gh, ctx):
     M.close()
 
 
+def test_batch_over_several_chunks_host_and_device(gh, ctx):
+    """70 source sets: more than the 64 queries of one pass, so the batch runs
+    in two chunks that reuse the first chunk's workspaces.  Host output (each
+    query's distances copied from its workspace before the next chunk runs)
+    and device output agree bit for bit, and with single solves."""
+    import torch
+    m = meshgen.noisy_icosphere(3, 12)
+    rng = meshgen.rng_for(77)
+    sets = [meshgen.random_sources(rng, m.nv, 1, 4) for _ in range(70)]
+    M = gh.Mesh(ctx, m.V, m.F)
+    prm = gh.params(gs_sweeps=60, form="face")
+    host = np.empty((len(sets), m.nv))
+    M.solve_batch(sets, host, prm)
+    dev = torch.empty((len(sets), m.nv), dtype=torch.float64, device="cuda")
+    M.solve_batch(sets, dev, prm)
+    assert np.array_equal(host, dev.cpu().numpy())
+    for q in (0, 63, 64, 69):
+        one = np.empty(m.nv)
+        M.solve(sets[q], one, prm)
+        assert np.array_equal(one, host[q]), q
+    M.close()
+
+
 def test_deterministic_and_device_buffers(gh, ctx):
     import torch
     m = meshgen.noisy_icosphere(4, 2)
