@@ -535,13 +535,20 @@ __global__ void k_increments(int nr, const int32_t *__restrict__ lorder, const i
     d[r] = dv;
 }
 
-// the distances in vertex order: +infinity where no source reaches
-__global__ void k_gather_d(int64_t nv, const int32_t *__restrict__ pos, const double *__restrict__ dpos,
-                           double *d) {
+// the distances in vertex order, +infinity where no source reaches, with the
+// last pointer-jumping round folded in: d_in / n_in are the chains before it
+// (after it every chain has reached its source)
+__global__ void k_gather_d(int64_t nv, const int32_t *__restrict__ pos, const double *__restrict__ d_in,
+                           const int32_t *__restrict__ n_in, double *d) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const int r = pos[v];
-    d[v] = (r >= 0) ? dpos[r] : __longlong_as_double(0x7ff0000000000000ll);
+    if (r < 0) {
+        d[v] = __longlong_as_double(0x7ff0000000000000ll);
+        return;
+    }
+    const int nx = n_in[r];
+    d[v] = (nx >= 0) ? d_in[r] + d_in[nx] : d_in[r];
 }
 
 // Sum of the increments along each vertex's chain of pairing vertices by
@@ -733,11 +740,11 @@ template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, d
     int rounds = 0;
     while ((1 << rounds) < q.nlev) ++rounds;
     int cur = 0;
-    for (int r = 0; r < rounds && nr > 0; ++r) {
+    for (int r = 0; r + 1 < rounds && nr > 0; ++r) {   // the last round runs inside the gather
         k_jump<<<blocks_for(nr, NT), NT, 0, st>>>(nr, d[cur], n[cur], d[cur ^ 1], n[cur ^ 1]); ++c->launches;
         cur ^= 1;
     }
-    k_gather_d<<<blocks_for(m.nv, NT), NT, 0, st>>>(m.nv, ptr<int32_t>(q.pos), d[cur], ptr<double>(q.d0));
+    k_gather_d<<<blocks_for(m.nv, NT), NT, 0, st>>>(m.nv, ptr<int32_t>(q.pos), d[cur], n[cur], ptr<double>(q.d0));
     ++c->launches;
     if (d_out) GH_CUDA(cudaMemcpyAsync(d_out, ptr<double>(q.d0), sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
     GH_CUDA(cudaGetLastError());
