@@ -478,6 +478,32 @@ PcDev pc_dev(const QueryWs &q) {
 
 // ------------------------------------------------------------------ integration
 
+// The integration's kernels run back to back on one stream, each a short pass
+// on the grid meshes.  They are launched as programmatic dependents: a block
+// signals, once its writes are issued, that the next kernel may be scheduled,
+// and the next kernel waits (griddepcontrol.wait: until the previous grid
+// has completed and its writes are visible) before it reads, so its launch
+// overlaps the previous kernel's tail instead of following it.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // increment of each vertex over its breadth-first pairing vertex k:
 // face form  1/|T| sum_{f in T_jk} g_f . (p_j - p_k)   (eq. IntegrationStep)
 // edge form  +x_e if v_j is the head of the orientation halfedge, else -x_e
@@ -500,6 +526,7 @@ __global__ void k_increments(int nr, const int32_t *__restrict__ lorder, const i
     if (level[v] == 0) {
         nxt[r] = -1;
         d[r] = 0.0;
+        griddep_launch_dependents();
         return;
     }
     const int p = parent[v];
@@ -533,6 +560,7 @@ __global__ void k_increments(int nr, const int32_t *__restrict__ lorder, const i
     }
     nxt[r] = pos[p];
     d[r] = dv;
+    griddep_launch_dependents();
 }
 
 // the distances in vertex order, +infinity where no source reaches, with the
@@ -543,6 +571,7 @@ __global__ void k_gather_d(int64_t nv, const int32_t *__restrict__ pos, const do
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const int r = pos[v];
+    griddep_wait();   // d_in and n_in come from the previous kernel
     if (r < 0) {
         d[v] = __longlong_as_double(0x7ff0000000000000ll);
         return;
@@ -559,6 +588,7 @@ __global__ void k_jump(int64_t nv, const double *__restrict__ d_in, const int32_
                        int32_t *n_out) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
+    griddep_wait();   // the inputs come from the previous kernel
     int nx = n_in[v];
     if (nx >= 0) {
         d_out[v] = d_in[v] + d_in[nx];
@@ -567,6 +597,7 @@ __global__ void k_jump(int64_t nv, const double *__restrict__ d_in, const int32_
         d_out[v] = d_in[v];
         n_out[v] = -1;
     }
+    griddep_launch_dependents();
 }
 
 // ------------------------------------------------------------------ heat residual
@@ -741,10 +772,13 @@ template <class T> gh_status integrate_t(Ctx *c, const DevMesh &m, QueryWs &q, d
     while ((1 << rounds) < q.nlev) ++rounds;
     int cur = 0;
     for (int r = 0; r + 1 < rounds && nr > 0; ++r) {   // the last round runs inside the gather
-        k_jump<<<blocks_for(nr, NT), NT, 0, st>>>(nr, d[cur], n[cur], d[cur ^ 1], n[cur ^ 1]); ++c->launches;
+        GH_CUDA(launch_dependent(k_jump, blocks_for(nr, NT), NT, st, (int64_t)nr, (const double *)d[cur],
+                                 (const int32_t *)n[cur], d[cur ^ 1], n[cur ^ 1]));
+        ++c->launches;
         cur ^= 1;
     }
-    k_gather_d<<<blocks_for(m.nv, NT), NT, 0, st>>>(m.nv, ptr<int32_t>(q.pos), d[cur], n[cur], ptr<double>(q.d0));
+    GH_CUDA(launch_dependent(k_gather_d, blocks_for(m.nv, NT), NT, st, (int64_t)m.nv, (const int32_t *)ptr<int32_t>(q.pos),
+                             (const double *)d[cur], (const int32_t *)n[cur], ptr<double>(q.d0)));
     ++c->launches;
     if (d_out) GH_CUDA(cudaMemcpyAsync(d_out, ptr<double>(q.d0), sizeof(double) * m.nv, cudaMemcpyDeviceToDevice, st));
     GH_CUDA(cudaGetLastError());
