@@ -11,6 +11,34 @@ namespace {
 
 constexpr int NT = 256;
 
+// The ADMM iterations and the integration are chains of short kernels on one
+// stream (a few microseconds each on the smaller meshes).  They are launched
+// as programmatic dependents: a block signals, once its writes are issued,
+// that the next kernel may be scheduled, and the next kernel waits
+// (griddepcontrol.wait: until the previous grid has completed and its writes
+// are visible) before its first read, so its launch overlaps the previous
+// kernel's tail instead of following it.  A kernel launched this way calls
+// griddep_wait before it touches memory that earlier kernels wrote.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <class T> __device__ __forceinline__ T ldexp_t(T x, int n);
 template <> __device__ __forceinline__ float ldexp_t<float>(float x, int n) { return ldexpf(x, n); }
 template <> __device__ __forceinline__ double ldexp_t<double>(double x, int n) { return ldexp(x, n); }
@@ -231,6 +259,7 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
                                                   const T *__restrict__ g_in, const T *__restrict__ q_in, T *g_out,
                                                   T *q_out, T mu, double *part, const AdmmCtl *ctl, int first,
                                                   const int32_t *__restrict__ pcm, const T *__restrict__ pcd) {
+    griddep_wait();
     if (ctl && ctl->stop) return;   // the residuals met the thresholds (the same for every thread)
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
@@ -272,6 +301,7 @@ __global__ void __launch_bounds__(NT) k_face_admm(int64_t nf, const int32_t *__r
         }
         if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
     }
+    griddep_launch_dependents();
 }
 
 // ------------------------------------------------------------------ edge ADMM
@@ -314,6 +344,7 @@ __global__ void k_edge_init(int64_t ne, const int32_t *__restrict__ edge_face, c
 template <class T>
 __global__ void k_edge_face_pass(int64_t nf, const int32_t *__restrict__ face_edge, const int8_t *__restrict__ sign,
                                  const T *__restrict__ x, T *w, T *lam, T mu, int do_lambda, const AdmmCtl *ctl) {
+    griddep_wait();
     if (ctl && ctl->stop) return;
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
@@ -331,6 +362,7 @@ __global__ void k_edge_face_pass(int64_t nf, const int32_t *__restrict__ face_ed
         qv += q[k] * v[k];
     }
     for (int k = 0; k < 3; ++k) w[3 * f + k] = v[k] - q[k] * qv / T(3);
+    griddep_launch_dependents();
 }
 
 // X-update (eq. xeupdate, edge_update); with multi-source path constraints
@@ -343,6 +375,7 @@ __global__ void __launch_bounds__(NT) k_edge_edge_pass(int64_t ne, const int32_t
                                                        const T *__restrict__ w, const T *__restrict__ lam, T *x, T mu,
                                                        double *part, const AdmmCtl *ctl,
                                                        const int32_t *__restrict__ pcm, const T *__restrict__ pcd) {
+    griddep_wait();
     if (ctl && ctl->stop) return;
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rp = 0.0, rd = 0.0;
@@ -380,6 +413,7 @@ __global__ void __launch_bounds__(NT) k_edge_edge_pass(int64_t ne, const int32_t
         }
         if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
     }
+    griddep_launch_dependents();
 }
 
 // sum per-block residual partials in a fixed order: out = sqrt(sum); NaN for
@@ -478,31 +512,6 @@ PcDev pc_dev(const QueryWs &q) {
 
 // ------------------------------------------------------------------ integration
 
-// The integration's kernels run back to back on one stream, each a short pass
-// on the grid meshes.  They are launched as programmatic dependents: a block
-// signals, once its writes are issued, that the next kernel may be scheduled,
-// and the next kernel waits (griddepcontrol.wait: until the previous grid
-// has completed and its writes are visible) before it reads, so its launch
-// overlaps the previous kernel's tail instead of following it.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
-                             Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
 
 // increment of each vertex over its breadth-first pairing vertex k:
 // face form  1/|T| sum_{f in T_jk} g_f . (p_j - p_k)   (eq. IntegrationStep)
@@ -696,9 +705,9 @@ template <class T> gh_status face_admm_t(Ctx *c, DevMesh &m, QueryWs &q, int ite
                                                   early ? ctl : nullptr); ++c->launches;
         }
         auto kern = m.intrinsic ? k_face_admm<T, true> : k_face_admm<T, false>;
-        kern<<<nb, NT, 0, st>>>(m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a], g[a ^ 1], qq[a ^ 1],
-                                (T)mu, part, early ? ctl : nullptr, it == 0, pc ? ptr<int32_t>(q.pc_map) : nullptr,
-                                pc ? ptr<T>(q.pc_delta) : nullptr);
+        GH_CUDA(launch_dependent(kern, nb, NT, st, (int64_t)m.nf, ptr<int32_t>(m.twin), rec, ptr<T>(q.h), g[a], qq[a],
+                                 g[a ^ 1], qq[a ^ 1], (T)mu, part, early ? ctl : nullptr, (int)(it == 0),
+                                 pc ? ptr<int32_t>(q.pc_map) : nullptr, pc ? ptr<T>(q.pc_delta) : nullptr));
         ++c->launches;
         if (part) {
             k_resid_final<<<1, NT, 0, st>>>(part, (int)nb, ptr<double>(q.resid) + 2 * it, early ? ctl : nullptr); ++c->launches;
@@ -734,17 +743,20 @@ template <class T> gh_status edge_admm_t(Ctx *c, const DevMesh &m, QueryWs &q, i
     const AdmmCtl *cx = early ? ctl : nullptr;
     const bool pc = q.pc_n > 0;
     for (int it = 0; it < iters; ++it) {
-        k_edge_face_pass<T><<<nbf, NT, 0, st>>>(m.nf, ptr<int32_t>(m.face_edge), ptr<int8_t>(m.face_sign),
-                                                ptr<T>(q.x), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, it > 0, cx); ++c->launches;
+        GH_CUDA(launch_dependent(k_edge_face_pass<T>, nbf, NT, st, (int64_t)m.nf, ptr<int32_t>(m.face_edge),
+                                 ptr<int8_t>(m.face_sign), ptr<T>(q.x), ptr<T>(q.w), ptr<T>(q.lam), (T)mu,
+                                 (int)(it > 0), cx));
+        ++c->launches;
         if (pc) {
             k_pc_project_edge<T><<<1, PJ, 0, st>>>(pc_dev(q), ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
                                                   ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), (T)mu, ptr<T>(q.pc_val),
                                                   ptr<T>(q.pc_delta), cx); ++c->launches;
         }
-        k_edge_edge_pass<T><<<nbe, NT, 0, st>>>(m.ne, ptr<int32_t>(m.edge_face), ptr<int32_t>(m.edge_slot),
-                                                ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x), (T)mu, part, cx,
-                                                pc ? ptr<int32_t>(q.pc_map) : nullptr,
-                                                pc ? ptr<T>(q.pc_delta) : nullptr); ++c->launches;
+        GH_CUDA(launch_dependent(k_edge_edge_pass<T>, nbe, NT, st, (int64_t)m.ne, ptr<int32_t>(m.edge_face),
+                                 ptr<int32_t>(m.edge_slot), ptr<T>(q.sz), ptr<T>(q.w), ptr<T>(q.lam), ptr<T>(q.x),
+                                 (T)mu, part, cx, pc ? ptr<int32_t>(q.pc_map) : nullptr,
+                                 pc ? ptr<T>(q.pc_delta) : nullptr));
+        ++c->launches;
         if (part) { k_resid_final<<<1, NT, 0, st>>>(part, (int)nbe, ptr<double>(q.resid) + 2 * it, cx); ++c->launches; }
         if (early) { k_admm_check<<<1, 1, 0, st>>>(ptr<double>(q.resid) + 2 * it, ctl, it); ++c->launches; }
     }
