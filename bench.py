@@ -274,24 +274,27 @@ def oracle_sample(md, src, m: float, sweeps_full: int, nv_full: int, sample_swee
     return est, t3 - t0
 
 
-def oracle_sample_setup():
-    """The sample mesh (the level-9 member of the benchmark's family), its
-    oracle data and source."""
+def oracle_sample_setup(workload: str = "c5"):
+    """The sample mesh, its oracle data and source: for the 168M-vertex line
+    the level-9 member of its family; for the grid line the grid itself
+    (the sample then bounds only the sweeps)."""
     import meshgen
     import oracle
     oracle.build()
-    w = meshgen.workload_c5(SAMPLE_LEVEL)
+    w = meshgen.workload_c2() if workload == "c2" else meshgen.workload_c5(SAMPLE_LEVEL)
     with oracle.parallel(True):
         md = oracle.mesh_data(w.mesh.V, w.mesh.F)
     return w, md
 
 
-def cpu_baseline(steps: int, warmup: int, nv_full: int, sweeps_full: int, m: float):
+def cpu_baseline(steps: int, warmup: int, nv_full: int, sweeps_full: int, m: float, workload: str = "c5"):
     """The level-parallel oracle on all host cores on the bounded sample.
     Returns (solves/s scaled to the full workload, seconds per sample step,
     description, cores)."""
     import oracle
-    w, md = oracle_sample_setup()
+    w, md = oracle_sample_setup(workload)
+    mesh_desc = (f"the jittered 1025^2 grid itself ({md.nv} V)" if workload == "c2" else
+                 f"the sinusoid icosphere of level {SAMPLE_LEVEL} ({md.nv} V)")
     src = w.sources[0]
     with oracle.parallel(True):
         cores = oracle.threads()
@@ -303,8 +306,8 @@ def cpu_baseline(steps: int, warmup: int, nv_full: int, sweeps_full: int, m: flo
             est.append(e)
             spent.append(s)
     sec = statistics.mean(est)
-    desc = (f"per step: the oracle's level-parallel build ({cores} threads) on the sinusoid icosphere of level "
-            f"{SAMPLE_LEVEL} ({md.nv} V), edge form, m = {m}: sets, {SAMPLE_SWEEPS} sweeps, normalise, {ADMM} ADMM "
+    desc = (f"per step: the oracle's level-parallel build ({cores} threads) on {mesh_desc}, "
+            f"edge form, m = {m}: sets, {SAMPLE_SWEEPS} sweeps, normalise, {ADMM} ADMM "
             f"iterations, integration; scaled to {nv_full} V and {sweeps_full} sweeps (sweeps by vertex-sweeps, "
             f"the rest by vertices); {statistics.mean(spent):.1f} s of CPU time per step")
     return 1.0 / sec, statistics.mean(spent), desc, cores
@@ -491,7 +494,7 @@ def run_ours(args):
                            "c4_small_meshes": serve_summary(g, local, small, 600, 4.0, 4300)}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            v, spent, sdesc, cores = cpu_baseline(1, 0, nv, sweeps, m)
+            v, spent, sdesc, cores = cpu_baseline(1, 0, nv, sweeps, m, args.workload)
             result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                       "sample": sdesc, "host": host_info()}
         print(json.dumps(result), flush=True)
