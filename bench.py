@@ -703,16 +703,23 @@ def run_reference(args):
     if rank != 0:
         return 0
     import meshgen
+    if args.workload not in ("c5", "c2"):
+        raise SystemExit("--impl reference times the default workload (c5) or the grid (c2)")
     if args.workload == "c2":
-        raise SystemExit("--impl reference times the default workload (c5)")
-    w5 = meshgen.workload_c5(args.level)
-    nv_full = w5.mesh.nv
-    sweeps = args.sweeps or w5.gs_edge
-    desc = (f"sinusoid icosphere level {args.level} ({nv_full} V, {w5.mesh.nf} F), one uniform random source, "
-            f"edge form, m = {w5.m}, {sweeps} Gauss-Seidel sweeps, {ADMM} ADMM iterations (1 solve per step)")
-    del w5
+        w2 = meshgen.workload_c2()
+        nv_full, sweeps, m = w2.mesh.nv, args.sweeps or C2_SWEEPS, 1.0
+        desc = (f"jittered grid 1025x1025 ({nv_full} V), one source, {sweeps} sweeps, edge form (the oracle's "
+                f"sample; the GPU line solves both forms)")
+        del w2
+    else:
+        w5 = meshgen.workload_c5(args.level)
+        nv_full = w5.mesh.nv
+        sweeps, m = args.sweeps or w5.gs_edge, 10.0
+        desc = (f"sinusoid icosphere level {args.level} ({nv_full} V, {w5.mesh.nf} F), one uniform random source, "
+                f"edge form, m = {w5.m}, {sweeps} Gauss-Seidel sweeps, {ADMM} ADMM iterations (1 solve per step)")
+        del w5
     t0 = time.perf_counter()
-    v, spent, sdesc, cores = cpu_baseline(args.steps, args.warmup, nv_full, sweeps, 10.0)
+    v, spent, sdesc, cores = cpu_baseline(args.steps, args.warmup, nv_full, sweeps, m, args.workload)
     wall = time.perf_counter() - t0
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * spent,
